@@ -1,0 +1,471 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 GGArray on the paper-shaped growth workload.
+
+One step is one pass of the whole hot path over one batch of synthetic input
+(1024 blocks x 512 threads, first bucket 4096 int32 elements):
+
+  clear (buckets back to the free lists) -> gga_insert of 512 rounds of
+  Uniform{0,1,2} per-thread insertions (~2^28 elements, 1 GiB) -> 2^26
+  random-index reads -> 2^26 random-index writes -> rw_b +1 sweep -> rw_g +1
+  sweep -> flatten into a contiguous array.
+
+`value` is elements inserted per second of step time (Gelem/s), inputs
+resident in HBM (larger than L2, so no flush is needed).  `e2e` repeats the
+step through the same C-ABI calls with the inputs copied from pinned host
+memory each step and the read results and the flattened array copied back.
+With torchrun, every rank grows its own replica (weak scaling, no data-path
+collective); the time is the max over ranks.
+
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload instead (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GGArray insert Gelem/s & % HBM roofline; mem/needed; served p99 latency"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+LAUNCHES_PER_STEP = {"clear": 2, "insert": 3, "read": 1, "write": 1, "rw_b": 1, "rw_g": 1, "flatten": 1}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--rounds", type=int, default=512, help="insertion rounds per step (512 = full workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (one process per GPU; no data-path collective).
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="gga_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = [float(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        try:
+            pw = max(float(r[3]) for r in rows)
+        except ValueError:
+            pw = None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": reasons,
+                "samples": len(rows), "power_w_max": pw}
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm.
+
+def algorithmic_bytes(N, R, L, T, E, n_rand):
+    """Bytes each phase must move at minimum (see the design notes)."""
+    counts = R * L * T * 4
+    return {
+        "insert": counts + 2 * N * E,          # counts read, values read, elements written
+        "read": n_rand * (8 + E + E),          # index, element, output
+        "write": n_rand * (8 + E + E),         # index, input, element
+        "rw_b": 2 * N * E,
+        "rw_g": 2 * N * E,
+        "flatten": 2 * N * E,
+    }
+
+
+def run_ours(args, world, rank, local):
+    from paper_2209_00103_gb300 import gga
+    from paper_2209_00103_gb300 import workloads as wl
+
+    w = wl.paper_growth()
+    R = args.rounds
+    spec = wl.InsertSpec(L=w.L, T=w.T, E=w.E, seed=w.spec.seed + 1000 * rank, dist=w.spec.dist, rounds=R,
+                         coeffs=w.spec.coeffs)
+    dev = torch.device("cuda", local)
+    counts, values = wl.make_insert_inputs_t(spec, dev)
+    N = int(values.shape[0])
+    n_rand = w.n_random if R == 512 else max(1, w.n_random * R // 512)
+    idx_r = wl.uniform_indices_t(w.read_seed, n_rand, N, dev)
+    idx_w = wl.uniform_indices_t(w.write_seed, n_rand, N, dev)
+    vals_w = wl.index_keyed_values_t(w.value_seed, idx_w, w.E)
+    out_r = gga.elem_tensor(n_rand, w.E, dev)
+    dst = gga.elem_tensor(N, w.E, dev)
+    pool_bytes = int(2.5 * N * w.E) + w.L * w.B * w.E * 4
+    g = gga.GGArray(w.L, w.T, w.B, w.E, pool_bytes)
+    stream = torch.cuda.current_stream(dev)
+
+    phases = ["clear", "insert", "read", "write", "rw_b", "rw_g", "flatten"]
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        g.clear(stream)
+        mark(1)
+        g.insert(counts, values, stream)
+        mark(2)
+        g.read(idx_r, out_r, stream)
+        mark(3)
+        g.write(idx_w, vals_w, stream)
+        mark(4)
+        g.sweep(gga.GGA_RW_B, 1, 1, stream)
+        mark(5)
+        g.sweep(gga.GGA_RW_G, 1, 1, stream)
+        mark(6)
+        g.flatten(dst, stream)
+        mark(7)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    n_check, rc = g.size(stream)
+    if rc != gga.GGA_OK or n_check != N:
+        raise RuntimeError(f"warm-up step failed: size {n_check} vs {N}, device error {rc}")
+    mem = g.memory(stream)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(8)] for _ in range(K)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    t0.record(stream)
+    for k in range(K):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier(world)
+    elapsed_ms = t0.elapsed_time(t1)
+    if g.last_error(stream) != gga.GGA_OK:
+        raise RuntimeError("device error during the timed steps")
+    t_max_ms = max_over_ranks(elapsed_ms, world)
+    total_elems = sum_over_ranks(float(N * K), world)
+    value = total_elems / (t_max_ms / 1e3) / 1e9
+
+    # Per-phase device times (ms, median over steps).
+    ph_ms = {}
+    for i, name in enumerate(phases):
+        ph_ms[name] = statistics.median(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(K))
+    peak, peak_src = peaks()
+    ab = algorithmic_bytes(N, R, w.L, w.T, w.E, n_rand)
+    phase_info = {}
+    for name in phases:
+        d = {"ms": round(ph_ms[name], 4)}
+        if name in ab:
+            gbs = ab[name] / (ph_ms[name] / 1e3) / 1e9
+            d.update({"algorithmic_bytes": ab[name], "achieved_gbs": round(gbs, 1),
+                      "frac_of_measured_peak": round(gbs / peak, 3), "frac_of_8tbs": round(gbs / 8000.0, 3)})
+        if name == "insert":
+            d["gelem_s"] = round(N / (ph_ms[name] / 1e3) / 1e9, 2)
+        phase_info[name] = d
+
+    # The dominant single-kernel phase by time carries the roofline record.
+    single = ["flatten", "rw_b", "rw_g", "read", "write"]
+    dom = max(["insert"] + single, key=lambda n: ph_ms[n])
+    kernels = {"insert": "count_scan_kernel + reserve_kernel + copy_kernel", "flatten": "flatten_kernel",
+               "rw_b": "sweep_b_kernel", "rw_g": "sweep_g_kernel", "read": "read_kernel", "write": "write_kernel"}
+    ach = ab[dom] / (ph_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 3), "traffic": None, "kernel": kernels[dom], "phase": dom,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src}
+    # Insert carries the headline roofline of the growable array itself.
+    ins_gbs = ab["insert"] / (ph_ms["insert"] / 1e3) / 1e9
+
+    # End to end through the C ABI with host buffers.
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world, dev, stream)
+
+    # In-kernel generated insertion (values drawn by the inserting threads).
+    gen = time_generated(w, R, pool_bytes, dev, stream)
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": round(t_max_ms / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"paper_growth_{w.L}x{w.T}_B{w.B}_int32_R{R}", "L": w.L, "T": w.T, "B": w.B,
+                   "elem_bytes": w.E, "rounds": R, "count_dist": "uniform{0,1,2}", "elements_per_gpu": N,
+                   "random_reads": n_rand, "random_writes": n_rand,
+                   "step": "clear+insert(all rounds, one call)+read+write+rw_b(+1)+rw_g(+1)+flatten",
+                   "l2": "inputs larger than L2 (counts and values 1 GiB each), no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "insert_roofline": {"achieved": round(ins_gbs, 1), "peak": peak, "unit": "GB/s",
+                            "frac": round(ins_gbs / peak, 3), "frac_of_8tbs": round(ins_gbs / 8000.0, 3),
+                            "gelem_s": phase_info["insert"]["gelem_s"]},
+        "phases": phase_info,
+        "mem_over_needed": round(mem["bucket_bytes"] / max(1, mem["live_bytes"]), 4),
+        "memory": mem,
+        "insert_generated": gen,
+        "gpu_launches": K * sum(LAUNCHES_PER_STEP.values()),
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(R)
+    g.close()
+    return result
+
+
+def run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world, dev, stream):
+    from paper_2209_00103_gb300 import gga
+    ins = [counts, values, idx_r, idx_w, vals_w]
+    host_in = [t.cpu().pin_memory() for t in ins]
+    host_out = [torch.empty(out_r.shape, dtype=out_r.dtype).pin_memory(),
+                torch.empty(dst.shape, dtype=dst.dtype).pin_memory()]
+    dev_in = [torch.empty_like(t) for t in ins]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+
+    def step():
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        g.clear(stream)
+        g.insert(dev_in[0], dev_in[1], stream)
+        g.read(dev_in[2], out_r, stream)
+        g.write(dev_in[3], dev_in[4], stream)
+        g.sweep(gga.GGA_RW_B, 1, 1, stream)
+        g.sweep(gga.GGA_RW_G, 1, 1, stream)
+        g.flatten(dst, stream)
+        host_out[0].copy_(out_r, non_blocking=True)
+        host_out[1].copy_(dst, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    K = args.e2e_steps
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(K):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(a.elapsed_time(b), world)
+    total = sum_over_ranks(float(N * K), world)
+    return {"value": round(total / (ms / 1e3) / 1e9, 3), "unit": "Gelem/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms / K, 3), "steps": K}
+
+
+def time_generated(w, R, pool_bytes, dev, stream):
+    from paper_2209_00103_gb300 import gga
+    g = gga.GGArray(w.L, w.T, w.B, w.E, pool_bytes)
+    spec = gga.make_gen_spec(w.spec.seed, w.spec.dist, w.spec.coeffs)
+    for _ in range(3):
+        g.clear(stream)
+        g.insert_generated(spec, R, stream)
+    torch.cuda.synchronize(dev)
+    n, rc = g.size(stream)
+    K = 10
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in evs:
+        g.clear(stream)
+        a.record(stream)
+        g.insert_generated(spec, R, stream)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+    g.close()
+    gbs = n * w.E / (ms / 1e3) / 1e9
+    peak, _ = peaks()
+    return {"elements": n, "ms": round(ms, 4), "gelem_s": round(n / (ms / 1e3) / 1e9, 2),
+            "achieved_gbs": round(gbs, 1), "frac_of_measured_peak": round(gbs / peak, 3),
+            "device_error": rc, "kernels": "gen_insert_kernel + finalize_kernel",
+            "algorithmic_bytes": "E per element (values drawn in registers, write only)"}
+
+
+# ---------------------------------------------------------------------------
+# The oracle arms (host cores).
+
+def oracle_sample(rounds: int):
+    """One bounded sample step of the workload on the CPU oracle; returns
+    (elements inserted, seconds, description)."""
+    import oracle
+    from paper_2209_00103_gb300 import workloads as wl
+    w = wl.paper_growth()
+    spec = wl.InsertSpec(L=w.L, T=w.T, E=w.E, seed=w.spec.seed, dist=w.spec.dist, rounds=rounds,
+                         coeffs=w.spec.coeffs)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    c_t, v_t = wl.make_insert_inputs_t(spec, dev)
+    counts = c_t.cpu().numpy().view(np.uint32)
+    values = v_t.cpu().numpy().view(np.uint32)
+    N = values.shape[0]
+    n_rand = max(1, w.n_random * rounds // 512)
+    idx_r = wl.uniform_indices(w.read_seed, n_rand, N)
+    idx_w = wl.uniform_indices(w.write_seed, n_rand, N)
+    vals_w = wl.index_keyed_values(w.value_seed, idx_w, w.E)
+    o = oracle.OracleGGArray(w.L, w.T, w.B, w.E)
+    t = time.perf_counter()
+    o.insert(counts, values)
+    o.read(idx_r)
+    o.write(idx_w, vals_w)
+    o.sweep_add(1, 1)
+    o.sweep_add(1, 1)
+    o.flatten()
+    dt = time.perf_counter() - t
+    o.close()
+    desc = (f"paper_growth 1024x512 B4096 int32 with {rounds} of 512 rounds ({N} elements), "
+            f"{n_rand} random reads and writes, two +1 sweeps, flatten; single-threaded C++ oracle")
+    return N, dt, desc
+
+
+def cpu_baseline(rounds_full: int):
+    rounds = max(1, min(rounds_full, 64))
+    N, dt, desc = oracle_sample(rounds)
+    return {"value": round(N / dt / 1e9, 5), "unit": "Gelem/s", "cores": 1, "kind": "oracle", "sample": desc,
+            "seconds": round(dt, 3), "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    # Size each step's sample so that warm-up + steps end within ~2 minutes.
+    N1, dt1, _ = oracle_sample(4)
+    per_round = dt1 / 4
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    rounds = int(max(1, min(args.rounds, budget / max(per_round, 1e-6))))
+    for _ in range(args.warmup):
+        oracle_sample(rounds)
+    tot_n, tot_t, desc = 0, 0.0, ""
+    for _ in range(args.steps):
+        n, dt, desc = oracle_sample(rounds)
+        tot_n += n
+        tot_t += dt
+    value = tot_n / tot_t / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gelem/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_t / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"paper_growth_1024x512_B4096_int32_R{args.rounds}", "sample_rounds": rounds},
+        "cpu_baseline": {"value": round(value, 5), "unit": "Gelem/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 5), "unit": "Gelem/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_ours(args, world, rank, local)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * gga.h -- C ABI of a GB300-native GGArray.
+ *
+ * A GGArray (Meneses, Navarro and Ferrada, "GGArray: A Dynamically Growable
+ * GPU Array", arXiv 2209.00103) is an array of LFVectors, one per thread
+ * block (Sec. IV, Fig. 1-2).  LFVector l is a list of buckets; bucket b holds
+ * B * 2^b elements (Algorithm 2) and is allocated only when an insertion
+ * reaches it (Algorithm 1).  Buckets never move once allocated.
+ *
+ * Conventions shared by every entry point:
+ *  - All data pointers are DEVICE pointers unless a parameter says "host".
+ *    The caller owns every buffer it passes; the handle owns its metadata and
+ *    its buckets.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call enqueues its work on `stream` and returns without
+ *    waiting, except where it says "synchronizes".  Calls on one handle must
+ *    be ordered on one stream (or otherwise serialised by the caller); calls
+ *    that overlap on the GPU race.
+ *  - Return value: GGA_OK, or an error code below.  Argument errors are found
+ *    on the host and nothing is enqueued.  Errors found by the GPU (pool
+ *    exhausted, index out of range, destination too small, count/value
+ *    mismatch) are latched in a device status word of the handle and
+ *    returned by the next synchronizing call (gga_size, gga_last_error).
+ *  - Element order: within an LFVector, elements appear round by round;
+ *    within a round by increasing thread id; a thread's elements are
+ *    contiguous (Sec. III-B: positions come from a prefix sum over the
+ *    block's threads).  The global order is LFVector-major (Sec. IV: the
+ *    prefix sum of LFVector sizes gives each LFVector's first global index).
+ */
+#ifndef GGA_H
+#define GGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GGA_OK = 0,
+  GGA_ERR_INVALID = 1,         /* bad argument, or (device) counts do not sum to n_values */
+  GGA_ERR_POOL_EXHAUSTED = 2,  /* (device) a bucket did not fit in the pool */
+  GGA_ERR_OUT_OF_RANGE = 3,    /* (device) read/write index >= size */
+  GGA_ERR_DST_TOO_SMALL = 4,   /* (device) flatten destination capacity < size */
+  GGA_ERR_CUDA = 5,            /* a CUDA runtime call failed */
+  GGA_ERR_TIMEOUT = 6          /* (device) a bounded wait gave up */
+};
+
+/* Sweep modes for gga_sweep (Sec. VI-B, rw_g and rw_b). */
+enum {
+  GGA_RW_G = 0,  /* one thread per element, global index -> (LFVector, bucket, offset) */
+  GGA_RW_B = 1   /* follows the block structure: bucket by bucket, no search */
+};
+
+/* Count distributions for gga_insert_generated. */
+enum {
+  GGA_DIST_BERNOULLI = 0,  /* Bernoulli(1/2): top bit of the draw */
+  GGA_DIST_UNIFORM3 = 1,   /* Uniform{0,1,2}: (hi32 * 3) >> 32 */
+  GGA_DIST_GEOMETRIC = 2,  /* Geometric(1/2) - 1: trailing one bits, at most 63 */
+  GGA_DIST_POISSON = 3     /* #{k : hi32 >= thresholds[k]} */
+};
+
+#define GGA_MAX_BUCKETS 48
+#define GGA_MAX_THRESHOLDS 16
+
+typedef struct gga_array* gga_handle;
+
+typedef struct {
+  uint32_t n_lfvectors;        /* L >= 1: LFVectors = thread blocks */
+  uint32_t threads_per_block;  /* T in [1, 1024]: threads inserting into one LFVector */
+  uint64_t base_bucket;        /* B: first bucket size in elements, a power of two */
+  uint32_t elem_bytes;         /* E: 4, 8 or 16 */
+  uint32_t reserved;           /* must be 0 */
+  uint64_t pool_bytes;         /* bytes of the bucket pool (HBM slab) */
+} gga_params;
+
+/* Counter-based draws for gga_insert_generated: thread t of block l
+ * (gtid = l*T + t) in round r draws h = SplitMix64 output number
+ * ((r << 32) | gtid) + 1 of the stream seeded with `seed`, i.e.
+ * mix64(seed + ((r << 32 | gtid) + 1) * 0x9E3779B97F4A7C15), takes a count c
+ * from h by `dist`, and inserts values va*gtid + vb*r + vc*k (k < c, mod 2^64)
+ * stored as E bytes: E=4 low 32 bits, E=8 all, E=16 the record
+ * {uint64 v, float(v & 0xFFFF), float((v >> 16) & 0xFFFF)}. */
+typedef struct {
+  uint64_t seed;
+  uint32_t dist;                             /* GGA_DIST_* */
+  uint32_t n_thresholds;                     /* for GGA_DIST_POISSON, <= 16 */
+  uint32_t thresholds[GGA_MAX_THRESHOLDS];
+  uint64_t va, vb, vc;
+  uint32_t round0;                           /* round number of the first round */
+  uint32_t reserved;
+} gga_gen_spec;
+
+/* Memory accounting returned by gga_memory (bytes). */
+typedef struct {
+  uint64_t bucket_bytes;     /* sum over LFVectors of capacity * E (Sec. V "memory used") */
+  uint64_t live_bytes;       /* size * E ("memory needed") */
+  uint64_t pool_bytes;       /* pool slab size */
+  uint64_t pool_bump_bytes;  /* slab bytes ever handed out by the bump pointer */
+  uint64_t free_list_bytes;  /* bytes parked on the per-size free lists */
+  uint64_t metadata_bytes;   /* descriptors, offsets, bucket tables, work lists */
+} gga_mem;
+
+/*
+ * gga_create -- make an empty GGArray (Sec. IV).
+ *  p        : parameters (host pointer, read during the call).
+ *  pool_dev : device slab of p->pool_bytes bytes to carve buckets from, 256-byte
+ *             aligned, borrowed (must outlive the handle); NULL = the handle
+ *             allocates its own slab.
+ *  out      : receives the handle (host pointer).
+ * Buckets are allocated lazily (Algorithm 1), so the new array holds no
+ * bucket.  Errors: GGA_ERR_INVALID (L = 0, T not in [1,1024], B not a power
+ * of two, E not in {4,8,16}, pool not aligned), GGA_ERR_CUDA.
+ */
+int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* out);
+
+/*
+ * gga_insert -- `rounds` rounds of block-level push_back (Algorithm 1).
+ *  counts_dev : uint32 [rounds][L][T]; counts[r][l][t] = elements thread t of
+ *               block l inserts in round r.
+ *  values_dev : n_values elements of E bytes, packed in (round, block, thread,
+ *               k) order -- the order the per-block prefix sums assign.
+ * Each round, each block reserves its run with one size update, allocates
+ * the buckets the run reaches (Algorithm 2, from the device pool), and the
+ * elements are written at their prefix-sum positions.  Then the global size
+ * and the prefix sum of LFVector sizes are updated (Sec. IV).
+ * Device errors: GGA_ERR_INVALID if the counts do not sum to n_values
+ * (nothing is inserted); GGA_ERR_POOL_EXHAUSTED if a bucket does not fit: the
+ * affected LFVector keeps the rounds that fit and drops the rest, other
+ * LFVectors are unaffected.  Scratch: the handle keeps a scratch buffer of
+ * about 16*rounds*L bytes and grows it (stream-ordered) when needed.
+ */
+int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
+               const void* values_dev, uint64_t n_values, void* stream);
+
+/*
+ * gga_insert_generated -- the same insertion with counts and values drawn
+ * inside the inserting threads (spec above), as a kernel calling push_back
+ * does.  spec is a host pointer.  Device errors as gga_insert.
+ */
+int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds, void* stream);
+
+/*
+ * gga_read -- out_dev[i] = element at global index idx_dev[i], i < n (rw_g
+ * addressing, Sec. VI-B: binary search over the prefix sum of sizes, then the
+ * bucket and offset of the LFVector-local index).  idx_dev: uint64 [n];
+ * out_dev: n elements of E bytes.  An index >= size latches
+ * GGA_ERR_OUT_OF_RANGE and its output element is zeroed.
+ */
+int gga_read(gga_handle h, const uint64_t* idx_dev, uint64_t n, void* out_dev, void* stream);
+
+/*
+ * gga_write -- element at global index idx_dev[i] = in_dev[i], i < n.
+ * Duplicate indices race (the GPU keeps one of the values); an index >= size
+ * latches GGA_ERR_OUT_OF_RANGE and is skipped.
+ */
+int gga_write(gga_handle h, const uint64_t* idx_dev, uint64_t n, const void* in_dev, void* stream);
+
+/*
+ * gga_sweep -- the r/w operation of Sec. VI-C: add `delta` to every element,
+ * `repeats` times (the paper adds +1 thirty times), elements taken as
+ * unsigned E-byte integers with wrap-around (E = 4 or 8; 16-byte records are
+ * GGA_ERR_INVALID).  mode GGA_RW_G visits elements by global index, GGA_RW_B
+ * by the block structure (Sec. VI-B).  Both give the same result.
+ */
+int gga_sweep(gga_handle h, int mode, uint64_t delta, uint32_t repeats, void* stream);
+
+/*
+ * gga_flatten -- copy the GGArray into the contiguous array dst_dev in global
+ * order (abstract and Sec. VI-C: insertion phase, then flatten, then regular
+ * r/w on a static array).  dst_dev holds dst_capacity_elems elements of E
+ * bytes and must be E-aligned.  If the size exceeds the capacity, nothing is
+ * copied and GGA_ERR_DST_TOO_SMALL is latched.  Buckets are streamed with
+ * TMA bulk copies.
+ */
+int gga_flatten(gga_handle h, void* dst_dev, uint64_t dst_capacity_elems, void* stream);
+
+/*
+ * gga_size -- global size and per-LFVector sizes/capacities (Sec. IV).
+ * Synchronizes `stream`.
+ *  total_host       : receives the global size (host pointer), may be NULL.
+ *  sizes_dev        : uint64 [L] per-LFVector sizes, or NULL.
+ *  caps_dev         : uint64 [L] capacities B*(2^nbuckets - 1), or NULL.
+ * Returns the latched device error, if any (it stays latched).
+ */
+int gga_size(gga_handle h, uint64_t* total_host, uint64_t* sizes_dev, uint64_t* caps_dev, void* stream);
+
+/* gga_offsets -- the prefix sum of LFVector sizes, uint64 [L+1] (Sec. IV). */
+int gga_offsets(gga_handle h, uint64_t* offsets_dev, void* stream);
+
+/*
+ * gga_clear -- empty the array: every bucket goes back to the pool's
+ * per-size free lists (reused by later insertions), sizes become 0.
+ */
+int gga_clear(gga_handle h, void* stream);
+
+/* gga_memory -- memory accounting (host pointer out).  Synchronizes. */
+int gga_memory(gga_handle h, gga_mem* out, void* stream);
+
+/* gga_last_error -- synchronize, return the latched device error and clear it. */
+int gga_last_error(gga_handle h, void* stream);
+
+/* gga_destroy -- free the handle's metadata and its own slab (a borrowed slab
+ * is left to its owner).  Synchronizes the device first. */
+int gga_destroy(gga_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GGA_H */

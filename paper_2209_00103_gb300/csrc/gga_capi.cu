@@ -1,0 +1,306 @@
+// gga_capi.cu -- the extern "C" entry points declared in include/gga.h.
+//
+// A handle owns one metadata allocation (sizes, offsets, bucket tables, work
+// lists, pool state, status words), an insertion scratch buffer that grows
+// stream-ordered when a call needs more rounds, and -- unless the caller lent
+// one -- the bucket slab.  Everything the operations compute runs in the
+// kernels of gga_insert.cu and gga_access.cu; this file checks arguments,
+// lays out memory and enqueues launches.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gga_core.cuh"
+
+namespace gga {
+uint64_t count_tiles(uint64_t n_rows, uint32_t T, bool vec_ok);
+}
+
+struct gga_array {
+  gga_params p;
+  uint32_t log2B;
+  int device;
+  int num_sms;
+  void* meta;
+  size_t meta_bytes;
+  void* slab;
+  bool own_slab;
+  void* scratch;
+  size_t scratch_bytes;
+  uint32_t scratch_rounds;
+  gga::ArrayView view;
+  gga::InsertScratch ins;   // pointers into meta (fixed part) and scratch (per-call part)
+  unsigned long long* memstats;
+};
+
+namespace {
+
+inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool valid_params(const gga_params* p) {
+  if (!p) return false;
+  if (p->n_lfvectors == 0 || p->threads_per_block == 0 || p->threads_per_block > 1024) return false;
+  if (p->base_bucket == 0 || (p->base_bucket & (p->base_bucket - 1)) != 0) return false;
+  if (p->base_bucket > (1ull << 40)) return false;
+  if (!(p->elem_bytes == 4 || p->elem_bytes == 8 || p->elem_bytes == 16)) return false;
+  if (p->reserved != 0) return false;
+  return true;
+}
+
+// Per-call scratch of gga_insert, laid out for up to R_cap rounds:
+// [look-back tile state | voff [rows+1] | pre [L][R+1]].  The tile state
+// sits first so that every call finds its (zeroed) part at the same place:
+// it is zeroed when the buffer is made and each insertion zeroes what it used.
+uint64_t max_tiles(uint32_t L, uint32_t T, uint32_t R) {
+  const uint64_t rows = static_cast<uint64_t>(R) * L;
+  const uint64_t a = gga::count_tiles(rows, T, false), b = gga::count_tiles(rows, T, true);
+  return a > b ? a : b;
+}
+
+size_t insert_scratch_bytes(uint32_t L, uint32_t T, uint32_t R) {
+  const uint64_t rows = static_cast<uint64_t>(R) * L;
+  size_t b = align_up(max_tiles(L, T, R) * 8 + 8, 256);
+  b += align_up((rows + 1) * 8, 256);
+  b += align_up(static_cast<uint64_t>(L) * (R + 1) * 8, 256);
+  return b;
+}
+
+void bind_scratch(gga_array* h, uint32_t R_cap, uint32_t R) {
+  const uint32_t L = h->p.n_lfvectors;
+  char* c = static_cast<char*>(h->scratch);
+  h->ins.tile_state = reinterpret_cast<unsigned long long*>(c);
+  c += align_up(max_tiles(L, h->p.threads_per_block, R_cap) * 8 + 8, 256);
+  h->ins.voff = reinterpret_cast<uint64_t*>(c);
+  c += align_up((static_cast<uint64_t>(R) * L + 1) * 8, 256);
+  h->ins.pre = reinterpret_cast<uint64_t*>(c);
+}
+
+int ensure_scratch(gga_array* h, uint32_t R, cudaStream_t st) {
+  if (R > h->scratch_rounds) {
+    uint32_t cap = h->scratch_rounds * 2 > R ? h->scratch_rounds * 2 : R;
+    const size_t nb = insert_scratch_bytes(h->p.n_lfvectors, h->p.threads_per_block, cap);
+    if (h->scratch && cudaFreeAsync(h->scratch, st) != cudaSuccess) return GGA_ERR_CUDA;
+    h->scratch = nullptr;
+    h->scratch_bytes = 0;
+    h->scratch_rounds = 0;
+    if (cudaMallocAsync(&h->scratch, nb, st) != cudaSuccess) return GGA_ERR_CUDA;
+    if (cudaMemsetAsync(h->scratch, 0, nb, st) != cudaSuccess) return GGA_ERR_CUDA;
+    h->scratch_bytes = nb;
+    h->scratch_rounds = cap;
+  }
+  bind_scratch(h, h->scratch_rounds, R);
+  return GGA_OK;
+}
+
+int sync_status(gga_array* h, cudaStream_t st, bool clear) {
+  uint32_t status = 0;
+  if (cudaMemcpyAsync(&status, h->view.status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GGA_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GGA_ERR_CUDA;
+  if (clear && status) {
+    if (cudaMemsetAsync(h->view.status, 0, 4, st) != cudaSuccess) return GGA_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GGA_ERR_CUDA;
+  }
+  return static_cast<int>(status);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* out) {
+  if (!out || !valid_params(p)) return GGA_ERR_INVALID;
+  if (pool_dev && (reinterpret_cast<uintptr_t>(pool_dev) & (gga::kGrain - 1)) != 0) return GGA_ERR_INVALID;
+  *out = nullptr;
+  cudaStream_t st = S(stream);
+  gga_array* h = new (std::nothrow) gga_array();
+  if (!h) return GGA_ERR_CUDA;
+  h->p = *p;
+  h->log2B = 0;
+  while ((1ull << h->log2B) < p->base_bucket) ++h->log2B;
+  if (cudaGetDevice(&h->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+    delete h;
+    return GGA_ERR_CUDA;
+  }
+  const uint64_t L = p->n_lfvectors;
+  // Metadata layout.
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_sizes = take(L * 8), o_offsets = take((L + 1) * 8), o_buckets = take(L * gga::kMaxBuckets * 8),
+               o_nb = take(L * 4), o_fl = take((L + 1) * 8), o_ib = take(L * 8), o_il = take(L * 8),
+               o_cp = take((L + 1) * 8), o_pool = take(sizeof(gga::PoolState)), o_status = take(4),
+               o_counters = take(16), o_mem = take(16);
+  h->meta_bytes = off;
+  if (cudaMalloc(&h->meta, h->meta_bytes) != cudaSuccess) {
+    delete h;
+    return GGA_ERR_CUDA;
+  }
+  char* m = static_cast<char*>(h->meta);
+  gga::ArrayView& v = h->view;
+  v.sizes = reinterpret_cast<uint64_t*>(m + o_sizes);
+  v.offsets = reinterpret_cast<uint64_t*>(m + o_offsets);
+  v.buckets = reinterpret_cast<uint64_t*>(m + o_buckets);
+  v.nbuckets = reinterpret_cast<uint32_t*>(m + o_nb);
+  v.fl_prefix = reinterpret_cast<uint64_t*>(m + o_fl);
+  v.pool = reinterpret_cast<gga::PoolState*>(m + o_pool);
+  v.status = reinterpret_cast<uint32_t*>(m + o_status);
+  v.B = p->base_bucket;
+  v.L = p->n_lfvectors;
+  v.T = p->threads_per_block;
+  v.E = p->elem_bytes;
+  v.log2B = h->log2B;
+  h->ins.ins_base = reinterpret_cast<uint64_t*>(m + o_ib);
+  h->ins.ins_len = reinterpret_cast<uint64_t*>(m + o_il);
+  h->ins.cp_prefix = reinterpret_cast<uint64_t*>(m + o_cp);
+  h->ins.counters = reinterpret_cast<uint32_t*>(m + o_counters);
+  h->memstats = reinterpret_cast<unsigned long long*>(m + o_mem);
+
+  // Slab.
+  h->own_slab = pool_dev == nullptr;
+  h->slab = pool_dev;
+  if (h->own_slab && p->pool_bytes > 0 && cudaMalloc(&h->slab, p->pool_bytes) != cudaSuccess) {
+    cudaFree(h->meta);
+    delete h;
+    return GGA_ERR_CUDA;
+  }
+  gga::PoolState ps;
+  std::memset(&ps, 0, sizeof(ps));
+  ps.bump = 0;
+  ps.cap = p->pool_bytes;
+  ps.base = reinterpret_cast<unsigned long long>(h->slab);
+  int rc = GGA_OK;
+  if (cudaMemsetAsync(h->meta, 0, h->meta_bytes, st) != cudaSuccess ||
+      cudaMemcpyAsync(v.pool, &ps, sizeof(ps), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = GGA_ERR_CUDA;
+  h->scratch = nullptr;
+  h->scratch_bytes = 0;
+  h->scratch_rounds = 0;
+  if (rc == GGA_OK) rc = ensure_scratch(h, 64, st);
+  if (rc == GGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (rc != GGA_OK) {
+    gga_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return GGA_OK;
+}
+
+int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds, const void* values_dev,
+               uint64_t n_values, void* stream) {
+  if (!h) return GGA_ERR_INVALID;
+  if (rounds == 0) return n_values == 0 ? GGA_OK : GGA_ERR_INVALID;
+  if (!counts_dev || (n_values > 0 && !values_dev)) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(values_dev) % h->p.elem_bytes) != 0 && n_values > 0) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(counts_dev) & 3) != 0) return GGA_ERR_INVALID;
+  cudaStream_t st = S(stream);
+  int rc = ensure_scratch(h, rounds, st);
+  if (rc != GGA_OK) return rc;
+  return gga::launch_insert(h->view, h->ins, counts_dev, rounds, values_dev, n_values, h->num_sms, st);
+}
+
+int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds, void* stream) {
+  if (!h || !spec) return GGA_ERR_INVALID;
+  if (spec->dist > GGA_DIST_POISSON || spec->n_thresholds > GGA_MAX_THRESHOLDS) return GGA_ERR_INVALID;
+  if (spec->dist == GGA_DIST_POISSON && spec->n_thresholds == 0) return GGA_ERR_INVALID;
+  if (rounds == 0) return GGA_OK;
+  return gga::launch_insert_generated(h->view, *spec, rounds, h->ins.counters, h->num_sms, S(stream));
+}
+
+int gga_read(gga_handle h, const uint64_t* idx_dev, uint64_t n, void* out_dev, void* stream) {
+  if (!h || (n > 0 && (!idx_dev || !out_dev))) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(out_dev) % h->p.elem_bytes) != 0) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(idx_dev) & 7) != 0) return GGA_ERR_INVALID;
+  return gga::launch_read(h->view, idx_dev, n, out_dev, h->num_sms, S(stream));
+}
+
+int gga_write(gga_handle h, const uint64_t* idx_dev, uint64_t n, const void* in_dev, void* stream) {
+  if (!h || (n > 0 && (!idx_dev || !in_dev))) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(in_dev) % h->p.elem_bytes) != 0) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(idx_dev) & 7) != 0) return GGA_ERR_INVALID;
+  return gga::launch_write(h->view, idx_dev, n, in_dev, h->num_sms, S(stream));
+}
+
+int gga_sweep(gga_handle h, int mode, uint64_t delta, uint32_t repeats, void* stream) {
+  if (!h || (mode != GGA_RW_G && mode != GGA_RW_B)) return GGA_ERR_INVALID;
+  if (h->p.elem_bytes == 16) return GGA_ERR_INVALID;
+  return gga::launch_sweep(h->view, mode, delta, repeats, h->num_sms, S(stream));
+}
+
+int gga_flatten(gga_handle h, void* dst_dev, uint64_t dst_capacity_elems, void* stream) {
+  if (!h || (!dst_dev && dst_capacity_elems > 0)) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(dst_dev) % h->p.elem_bytes) != 0) return GGA_ERR_INVALID;
+  return gga::launch_flatten(h->view, dst_dev, dst_capacity_elems, h->num_sms, S(stream));
+}
+
+int gga_size(gga_handle h, uint64_t* total_host, uint64_t* sizes_dev, uint64_t* caps_dev, void* stream) {
+  if (!h) return GGA_ERR_INVALID;
+  cudaStream_t st = S(stream);
+  const uint32_t L = h->p.n_lfvectors;
+  if (sizes_dev &&
+      cudaMemcpyAsync(sizes_dev, h->view.sizes, L * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return GGA_ERR_CUDA;
+  if (caps_dev && gga::launch_caps(h->view, caps_dev, st) != GGA_OK) return GGA_ERR_CUDA;
+  uint64_t n = 0;
+  if (cudaMemcpyAsync(&n, h->view.offsets + L, sizeof(uint64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return GGA_ERR_CUDA;
+  const int rc = sync_status(h, st, false);
+  if (total_host) *total_host = n;
+  return rc;
+}
+
+int gga_offsets(gga_handle h, uint64_t* offsets_dev, void* stream) {
+  if (!h || !offsets_dev) return GGA_ERR_INVALID;
+  return cudaMemcpyAsync(offsets_dev, h->view.offsets, (h->p.n_lfvectors + 1ull) * sizeof(uint64_t),
+                         cudaMemcpyDeviceToDevice, S(stream)) == cudaSuccess
+             ? GGA_OK
+             : GGA_ERR_CUDA;
+}
+
+int gga_clear(gga_handle h, void* stream) {
+  if (!h) return GGA_ERR_INVALID;
+  return gga::launch_clear(h->view, S(stream));
+}
+
+int gga_memory(gga_handle h, gga_mem* out, void* stream) {
+  if (!h || !out) return GGA_ERR_INVALID;
+  cudaStream_t st = S(stream);
+  if (cudaMemsetAsync(h->memstats, 0, 16, st) != cudaSuccess) return GGA_ERR_CUDA;
+  if (gga::launch_memory(h->view, reinterpret_cast<uint64_t*>(h->memstats), st) != GGA_OK) return GGA_ERR_CUDA;
+  unsigned long long ms[2];
+  gga::PoolState ps;
+  if (cudaMemcpyAsync(ms, h->memstats, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&ps, h->view.pool, sizeof(ps), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GGA_ERR_CUDA;
+  out->bucket_bytes = ms[0];
+  out->live_bytes = ms[1];
+  out->pool_bytes = h->p.pool_bytes;
+  out->pool_bump_bytes = ps.bump;
+  out->free_list_bytes = ps.free_bytes;
+  out->metadata_bytes = h->meta_bytes;
+  return GGA_OK;
+}
+
+int gga_last_error(gga_handle h, void* stream) {
+  if (!h) return GGA_ERR_INVALID;
+  return sync_status(h, S(stream), true);
+}
+
+int gga_destroy(gga_handle h) {
+  if (!h) return GGA_ERR_INVALID;
+  int rc = GGA_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (h->scratch && cudaFree(h->scratch) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (h->own_slab && h->slab && cudaFree(h->slab) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (h->meta && cudaFree(h->meta) != cudaSuccess) rc = GGA_ERR_CUDA;
+  delete h;
+  return rc;
+}
+
+}  // extern "C"

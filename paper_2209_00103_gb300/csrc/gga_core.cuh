@@ -1,0 +1,311 @@
+// gga_core.cuh -- device-side building blocks of the GB300 GGArray.
+//
+// Layout in HBM (one set per handle):
+//   sizes    [L]        uint64  LFVector sizes
+//   offsets  [L+1]      uint64  prefix sum of sizes (Sec. IV), offsets[L] = N
+//   buckets  [L][48]    uint64  bucket base addresses, 0 = nil (Algorithm 1)
+//   nbuckets [L]        uint32  buckets allocated so far (always a prefix)
+//   pool                PoolState: bump pointer + per-size free lists
+//   status              uint32  first device-detected error
+// Buckets live in one pre-reserved slab; bucket b of every LFVector holds
+// B * 2^b elements (Algorithm 2) and starts on a 256-byte boundary.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gga.h"
+
+namespace gga {
+
+constexpr int kMaxBuckets = GGA_MAX_BUCKETS;
+constexpr int kPoolClasses = 64;
+constexpr uint64_t kGrain = 256;             // bucket alignment / allocation granule
+constexpr uint64_t kUnitMask = (1ull << 40) - 1;
+constexpr uint32_t kCasLimit = 1u << 20;     // bound on lock-free retry loops
+constexpr uint32_t kSpinLimit = 1u << 22;    // bound on spin waits (~0.5 s with backoff)
+constexpr uint32_t kChunkBytes = 16384;      // flatten / rw_b work unit
+
+struct PoolState {
+  unsigned long long bump;                      // slab bytes handed out so far
+  unsigned long long cap;                       // slab bytes
+  unsigned long long base;                      // slab address
+  unsigned long long free_head[kPoolClasses];   // (unit + 1) | tag << 40, unit = 256 B
+  unsigned long long free_bytes;                // bytes parked on the free lists
+};
+
+struct ArrayView {
+  uint64_t* sizes;
+  uint64_t* offsets;
+  uint64_t* buckets;
+  uint32_t* nbuckets;
+  PoolState* pool;
+  uint32_t* status;
+  uint64_t* fl_prefix;   // [L+1] prefix of 16 KB bucket chunks per LFVector (flatten, rw_b)
+  uint64_t B;
+  uint32_t L, T, E, log2B;
+};
+
+// ---------------------------------------------------------------------------
+// Errors.
+
+__device__ __forceinline__ void latch_error(uint32_t* status, uint32_t code) {
+  atomicCAS(status, 0u, code);
+}
+
+// ---------------------------------------------------------------------------
+// Index math (Algorithm 2 bucket sizes): LFVector-local index j lies in
+// bucket b with B(2^b - 1) <= j < B(2^(b+1) - 1), i.e. B*2^b <= j + B <
+// B*2^(b+1).  So the highest set bit of j + B is log2(B) + b, and the offset
+// is (j + B) - 2^hb.  No loop.
+
+__device__ __forceinline__ void bucket_of(uint64_t j, uint32_t log2B, uint32_t& b, uint64_t& off) {
+  const uint64_t x = j + (1ull << log2B);
+  const uint32_t hb = 63u - static_cast<uint32_t>(__clzll(static_cast<long long>(x)));
+  b = hb - log2B;
+  off = x - (1ull << hb);
+}
+
+__host__ __device__ __forceinline__ uint64_t bucket_first(uint32_t b, uint32_t log2B) {
+  return ((1ull << b) - 1ull) << log2B;   // B (2^b - 1)
+}
+
+__host__ __device__ __forceinline__ uint64_t bucket_len(uint32_t b, uint32_t log2B) {
+  return 1ull << (log2B + b);             // B 2^b
+}
+
+// Number of buckets reached by indices 0..size-1.
+__device__ __forceinline__ uint32_t buckets_for(uint64_t size, uint32_t log2B) {
+  if (size == 0) return 0;
+  uint32_t b;
+  uint64_t off;
+  bucket_of(size - 1, log2B, b, off);
+  return b + 1;
+}
+
+// upper_bound over a sorted uint64 array a[0..n): first i with a[i] > x.
+__device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* a, uint32_t n, uint64_t x) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Warp / block scans (Sec. III-B: shuffle prefix sum inside the block).
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_incl_scan(V v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const V n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Device pool (Algorithm 2's malloc): bump pointer over the slab, plus one
+// intrusive free list per power-of-two size class.  A free bucket stores the
+// next free unit in its first 8 bytes.  Pops happen only in insertion
+// kernels and pushes only in gga_clear, never in the same kernel, so the
+// Treiber stacks see no ABA; the tag is kept anyway.
+
+__device__ __forceinline__ uint64_t alloc_bytes_for(uint64_t bytes) {
+  return bytes < kGrain ? kGrain : bytes;   // bucket sizes are powers of two
+}
+
+__device__ inline uint64_t pool_alloc(PoolState* p, uint64_t bytes, uint32_t* status) {
+  bytes = alloc_bytes_for(bytes);
+  const int cls = 63 - __clzll(static_cast<long long>(bytes));
+  unsigned long long head = *reinterpret_cast<volatile unsigned long long*>(&p->free_head[cls]);
+  for (uint32_t it = 0; it < kCasLimit; ++it) {
+    const uint64_t unit = head & kUnitMask;
+    if (unit == 0) break;
+    const uint64_t addr = p->base + (unit - 1) * kGrain;
+    const uint64_t next = *reinterpret_cast<volatile unsigned long long*>(addr) & kUnitMask;
+    const unsigned long long nh = next | (((head >> 40) + 1) << 40);
+    const unsigned long long prev = atomicCAS(&p->free_head[cls], head, nh);
+    if (prev == head) {
+      atomicAdd(&p->free_bytes, static_cast<unsigned long long>(0ull - bytes));
+      return addr;
+    }
+    head = prev;
+  }
+  unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&p->bump);
+  for (uint32_t it = 0; it < kCasLimit; ++it) {
+    if (cur + bytes > p->cap) return 0;
+    const unsigned long long prev = atomicCAS(&p->bump, cur, cur + bytes);
+    if (prev == cur) return p->base + cur;
+    cur = prev;
+  }
+  latch_error(status, GGA_ERR_TIMEOUT);
+  return 0;
+}
+
+__device__ inline void pool_free(PoolState* p, uint64_t addr, uint64_t bytes, uint32_t* status) {
+  bytes = alloc_bytes_for(bytes);
+  const int cls = 63 - __clzll(static_cast<long long>(bytes));
+  const uint64_t unit = (addr - p->base) / kGrain + 1;
+  unsigned long long head = *reinterpret_cast<volatile unsigned long long*>(&p->free_head[cls]);
+  for (uint32_t it = 0; it < kCasLimit; ++it) {
+    *reinterpret_cast<volatile unsigned long long*>(addr) = head & kUnitMask;
+    __threadfence();
+    const unsigned long long nh = unit | (((head >> 40) + 1) << 40);
+    const unsigned long long prev = atomicCAS(&p->free_head[cls], head, nh);
+    if (prev == head) {
+      atomicAdd(&p->free_bytes, static_cast<unsigned long long>(bytes));
+      return;
+    }
+    head = prev;
+  }
+  latch_error(status, GGA_ERR_TIMEOUT);
+}
+
+// Allocate buckets nb..need-1 of LFVector l.  Returns the number of buckets
+// allocated afterwards (== need on success).
+__device__ inline uint32_t grow_buckets(const ArrayView& v, uint32_t l, uint32_t nb, uint32_t need) {
+  for (uint32_t b = nb; b < need; ++b) {
+    if (b >= static_cast<uint32_t>(kMaxBuckets)) return b;
+    const uint64_t addr = pool_alloc(v.pool, bucket_len(b, v.log2B) * v.E, v.status);
+    if (addr == 0) return b;
+    v.buckets[static_cast<uint64_t>(l) * kMaxBuckets + b] = addr;
+  }
+  return need;
+}
+
+// Chunks of kChunkBytes covering the live part of LFVector of `size`
+// elements, bucket by bucket (flatten / rw_b work units).
+__device__ __forceinline__ uint64_t bucket_chunks(uint64_t size, uint32_t log2B, uint32_t E) {
+  uint64_t n = 0;
+  for (uint32_t b = 0; b < static_cast<uint32_t>(kMaxBuckets); ++b) {
+    const uint64_t first = bucket_first(b, log2B);
+    if (first >= size) break;
+    uint64_t len = bucket_len(b, log2B);
+    if (size - first < len) len = size - first;
+    n += (len * E + kChunkBytes - 1) / kChunkBytes;
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers: mbarrier and bulk (non-tensor) TMA copies.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  return false;
+}
+
+// Global -> shared bulk copy completing on an mbarrier.  16-byte aligned
+// addresses, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared -> global bulk copy tracked by bulk groups.
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* smem_src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(smem_src)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Element types by size.
+
+template <int E> struct Elem;
+template <> struct Elem<4> { typedef uint32_t T; };
+template <> struct Elem<8> { typedef unsigned long long T; };
+template <> struct Elem<16> { typedef uint4 T; };
+
+// 16 bytes seen as E-byte elements or as one 128-bit word.
+template <int E>
+union Vec16 {
+  typename Elem<E>::T e[16 / E];
+  uint4 v;
+};
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in the .cu files).
+
+struct InsertScratch {
+  uint64_t* voff;                 // [n_rows + 1] value offset of every (round, block) run
+  uint64_t* pre;                  // [L][R + 1] run start of every round, relative to the batch base
+  unsigned long long* tile_state; // [n_tiles] decoupled look-back state
+  uint64_t* ins_base;             // [L] LFVector size before the batch
+  uint64_t* ins_len;              // [L] committed elements of the batch
+  uint64_t* cp_prefix;            // [L+1] prefix of copy chunks
+  uint32_t* counters;             // [0] tile ticket, [1] done counter
+};
+
+int launch_insert(const ArrayView& v, const InsertScratch& s, const uint32_t* counts, uint32_t rounds,
+                  const void* values, uint64_t n_values, int num_sms, cudaStream_t st);
+int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32_t rounds,
+                            uint32_t* done_counter, int num_sms, cudaStream_t st);
+int launch_finalize(const ArrayView& v, cudaStream_t st);
+int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st);
+int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms,
+                 cudaStream_t st);
+int launch_sweep(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms, cudaStream_t st);
+int launch_flatten(const ArrayView& v, void* dst, uint64_t cap_elems, int num_sms, cudaStream_t st);
+int launch_clear(const ArrayView& v, cudaStream_t st);
+int launch_caps(const ArrayView& v, uint64_t* caps, cudaStream_t st);
+int launch_memory(const ArrayView& v, uint64_t* out2, cudaStream_t st);
+
+}  // namespace gga

@@ -1,0 +1,296 @@
+"""Thin ctypes binding of the C ABI in include/gga.h.
+
+Argument marshalling only: every operation runs in the CUDA kernels of
+libgga.so.  Tensors are passed as raw device pointers (``data_ptr()``) and
+streams as their ``cuda_stream`` handle; PyTorch serves only as the device
+memory and stream provider.  If libgga.so is missing or fails to load, the
+import raises -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+GGA_OK = 0
+GGA_ERR_INVALID = 1
+GGA_ERR_POOL_EXHAUSTED = 2
+GGA_ERR_OUT_OF_RANGE = 3
+GGA_ERR_DST_TOO_SMALL = 4
+GGA_ERR_CUDA = 5
+GGA_ERR_TIMEOUT = 6
+ERROR_NAMES = {0: "OK", 1: "INVALID", 2: "POOL_EXHAUSTED", 3: "OUT_OF_RANGE",
+               4: "DST_TOO_SMALL", 5: "CUDA", 6: "TIMEOUT"}
+
+GGA_RW_G = 0
+GGA_RW_B = 1
+DIST = {"bernoulli": 0, "uniform3": 1, "geometric": 2, "poisson": 3}
+MAX_THRESHOLDS = 16
+
+# Every symbol include/gga.h declares.
+EXPORTED = ["gga_create", "gga_insert", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
+            "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
+            "gga_destroy"]
+
+
+class gga_params(ctypes.Structure):
+    _fields_ = [("n_lfvectors", ctypes.c_uint32), ("threads_per_block", ctypes.c_uint32),
+                ("base_bucket", ctypes.c_uint64), ("elem_bytes", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("pool_bytes", ctypes.c_uint64)]
+
+
+class gga_gen_spec(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("dist", ctypes.c_uint32), ("n_thresholds", ctypes.c_uint32),
+                ("thresholds", ctypes.c_uint32 * MAX_THRESHOLDS), ("va", ctypes.c_uint64),
+                ("vb", ctypes.c_uint64), ("vc", ctypes.c_uint64), ("round0", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class gga_mem(ctypes.Structure):
+    _fields_ = [("bucket_bytes", ctypes.c_uint64), ("live_bytes", ctypes.c_uint64),
+                ("pool_bytes", ctypes.c_uint64), ("pool_bump_bytes", ctypes.c_uint64),
+                ("free_list_bytes", ctypes.c_uint64), ("metadata_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgga.so (building it with nvcc first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"libgga.so not built ({path})")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "gga_create": [ctypes.POINTER(gga_params), vp, vp, ctypes.POINTER(vp)],
+        "gga_insert": [vp, vp, u32, vp, u64, vp],
+        "gga_insert_generated": [vp, ctypes.POINTER(gga_gen_spec), u32, vp],
+        "gga_read": [vp, vp, u64, vp, vp],
+        "gga_write": [vp, vp, u64, vp, vp],
+        "gga_sweep": [vp, i32, u64, u32, vp],
+        "gga_flatten": [vp, vp, u64, vp],
+        "gga_size": [vp, ctypes.POINTER(u64), vp, vp, vp],
+        "gga_offsets": [vp, vp, vp],
+        "gga_clear": [vp, vp],
+        "gga_memory": [vp, ctypes.POINTER(gga_mem), vp],
+        "gga_last_error": [vp, vp],
+        "gga_destroy": [vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class GGAError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what} failed: GGA_ERR_{ERROR_NAMES.get(code, code)}")
+        self.code = code
+
+
+def _check(rc: int, what: str):
+    if rc != GGA_OK:
+        raise GGAError(rc, what)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_ELEM_DTYPE = {4: torch.int32, 8: torch.int64, 16: torch.int64}
+
+
+def elem_tensor(n: int, E: int, device="cuda") -> torch.Tensor:
+    """A device buffer of n E-byte elements (int32, int64, or int64 pairs for records)."""
+    if E == 16:
+        return torch.empty((n, 2), dtype=torch.int64, device=device)
+    return torch.empty(n, dtype=_ELEM_DTYPE[E], device=device)
+
+
+# ---------------------------------------------------------------------------
+# Functions with the C names (argument marshalling only).
+
+def gga_create(L: int, T: int, B: int, E: int, pool_bytes: int, pool: torch.Tensor | None = None,
+               stream=None) -> ctypes.c_void_p:
+    lib = load_library()
+    p = gga_params(L, T, B, E, 0, pool_bytes)
+    h = ctypes.c_void_p()
+    _check(lib.gga_create(ctypes.byref(p), _dptr(pool) if pool is not None else None, _stream(stream),
+                          ctypes.byref(h)), "gga_create")
+    return h
+
+
+def gga_insert(h, counts: torch.Tensor, values: torch.Tensor, stream=None):
+    assert counts.dtype in (torch.int32, torch.uint32) and counts.dim() == 3
+    n_values = values.shape[0] if values.numel() else 0
+    _check(load_library().gga_insert(h, _dptr(counts), counts.shape[0], _dptr(values) if n_values else None,
+                                     n_values, _stream(stream)), "gga_insert")
+
+
+def make_gen_spec(seed: int, dist: str, coeffs, round0: int = 0, thresholds=None) -> gga_gen_spec:
+    s = gga_gen_spec()
+    s.seed = seed & 0xFFFFFFFFFFFFFFFF
+    s.dist = DIST[dist]
+    thr = [] if thresholds is None else [int(x) for x in thresholds]
+    assert len(thr) <= MAX_THRESHOLDS
+    s.n_thresholds = len(thr)
+    for i, x in enumerate(thr):
+        s.thresholds[i] = x
+    va, vb, vc = (int(c) & 0xFFFFFFFFFFFFFFFF for c in coeffs)
+    s.va, s.vb, s.vc = va, vb, vc
+    s.round0 = round0
+    return s
+
+
+def gga_insert_generated(h, spec: gga_gen_spec, rounds: int, stream=None):
+    _check(load_library().gga_insert_generated(h, ctypes.byref(spec), rounds, _stream(stream)),
+           "gga_insert_generated")
+
+
+def gga_read(h, idx: torch.Tensor, out: torch.Tensor, stream=None):
+    assert idx.dtype in (torch.int64, torch.uint64)
+    _check(load_library().gga_read(h, _dptr(idx), idx.shape[0], _dptr(out), _stream(stream)), "gga_read")
+
+
+def gga_write(h, idx: torch.Tensor, vals: torch.Tensor, stream=None):
+    assert idx.dtype in (torch.int64, torch.uint64)
+    _check(load_library().gga_write(h, _dptr(idx), idx.shape[0], _dptr(vals), _stream(stream)), "gga_write")
+
+
+def gga_sweep(h, mode: int, delta: int, repeats: int = 1, stream=None):
+    _check(load_library().gga_sweep(h, mode, delta & 0xFFFFFFFFFFFFFFFF, repeats, _stream(stream)), "gga_sweep")
+
+
+def gga_flatten(h, dst: torch.Tensor, capacity: int | None = None, stream=None):
+    cap = dst.shape[0] if capacity is None else capacity
+    _check(load_library().gga_flatten(h, _dptr(dst), cap, _stream(stream)), "gga_flatten")
+
+
+def gga_size(h, sizes: torch.Tensor | None = None, caps: torch.Tensor | None = None, stream=None):
+    """Returns (total, device_error_code).  Synchronizes the stream."""
+    n = ctypes.c_uint64(0)
+    rc = load_library().gga_size(h, ctypes.byref(n), _dptr(sizes) if sizes is not None else None,
+                                 _dptr(caps) if caps is not None else None, _stream(stream))
+    if rc == GGA_ERR_CUDA:
+        raise GGAError(rc, "gga_size")
+    return int(n.value), rc
+
+
+def gga_offsets(h, out: torch.Tensor, stream=None):
+    _check(load_library().gga_offsets(h, _dptr(out), _stream(stream)), "gga_offsets")
+
+
+def gga_clear(h, stream=None):
+    _check(load_library().gga_clear(h, _stream(stream)), "gga_clear")
+
+
+def gga_memory(h, stream=None) -> dict:
+    m = gga_mem()
+    _check(load_library().gga_memory(h, ctypes.byref(m), _stream(stream)), "gga_memory")
+    return {k: int(getattr(m, k)) for k, _ in gga_mem._fields_}
+
+
+def gga_last_error(h, stream=None) -> int:
+    return int(load_library().gga_last_error(h, _stream(stream)))
+
+
+def gga_destroy(h):
+    _check(load_library().gga_destroy(h), "gga_destroy")
+
+
+# ---------------------------------------------------------------------------
+# Object wrapper.
+
+class GGArray:
+    """A GGArray on the current CUDA device (L LFVectors of T-thread blocks,
+    first bucket B elements, E-byte elements, bucket pool of pool_bytes)."""
+
+    def __init__(self, L: int, T: int, B: int, E: int, pool_bytes: int, pool: torch.Tensor | None = None,
+                 stream=None):
+        self.L, self.T, self.B, self.E = L, T, B, E
+        self.pool_bytes = pool_bytes
+        self._pool = pool
+        self.h = gga_create(L, T, B, E, pool_bytes, pool, stream)
+
+    def insert(self, counts, values, stream=None):
+        gga_insert(self.h, counts, values, stream)
+
+    def insert_generated(self, spec, rounds, stream=None):
+        gga_insert_generated(self.h, spec, rounds, stream)
+
+    def read(self, idx, out=None, stream=None):
+        if out is None:
+            out = elem_tensor(idx.shape[0], self.E, idx.device)
+        gga_read(self.h, idx, out, stream)
+        return out
+
+    def write(self, idx, vals, stream=None):
+        gga_write(self.h, idx, vals, stream)
+
+    def sweep(self, mode, delta=1, repeats=1, stream=None):
+        gga_sweep(self.h, mode, delta, repeats, stream)
+
+    def flatten(self, dst=None, stream=None):
+        if dst is None:
+            n, _ = self.size(stream)
+            dst = elem_tensor(max(n, 1), self.E)
+        gga_flatten(self.h, dst, dst.shape[0], stream)
+        return dst
+
+    def size(self, stream=None):
+        return gga_size(self.h, stream=stream)
+
+    def sizes_caps(self, stream=None):
+        sizes = torch.empty(self.L, dtype=torch.int64, device="cuda")
+        caps = torch.empty(self.L, dtype=torch.int64, device="cuda")
+        n, rc = gga_size(self.h, sizes, caps, stream)
+        return n, rc, sizes, caps
+
+    def offsets(self, stream=None):
+        out = torch.empty(self.L + 1, dtype=torch.int64, device="cuda")
+        gga_offsets(self.h, out, stream)
+        return out
+
+    def clear(self, stream=None):
+        gga_clear(self.h, stream)
+
+    def memory(self, stream=None):
+        return gga_memory(self.h, stream)
+
+    def last_error(self, stream=None):
+        return gga_last_error(self.h, stream)
+
+    def close(self):
+        if self.h:
+            gga_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

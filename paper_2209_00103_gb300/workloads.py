@@ -220,3 +220,94 @@ def scaled_growth(rounds: int, L: int = 1024, T: int = 512, B: int = 4096) -> Gr
     return GrowthWorkload(f"paper_growth_{L}x{T}_B{B}_int32_R{rounds}", L, T, B, 4, spec,
                           n_random=min(1 << 26, L * T * rounds // 4 + 1),
                           read_seed=201, write_seed=202, value_seed=203)
+
+
+# ---------------------------------------------------------------------------
+# The same generator on torch tensors (any device), so full-size inputs can be
+# drawn directly in device memory.  Bit patterns are carried in int64 tensors
+# with wrap-around arithmetic; right shifts are made logical by masking.
+
+def _s64(u: int) -> int:
+    u &= MASK64
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def _lsr(x, s: int):
+    return (x >> s) & ((1 << (64 - s)) - 1)
+
+
+def mix64_t(z):
+    z = (z ^ _lsr(z, 30)) * _s64(0xBF58476D1CE4E5B9)
+    z = (z ^ _lsr(z, 27)) * _s64(0x94D049BB133111EB)
+    return z ^ _lsr(z, 31)
+
+
+def splitmix_at_t(seed: int, keys):
+    """Torch twin of splitmix_at: keys int64 tensor -> int64 tensor of draws."""
+    return mix64_t(_s64(seed) + (keys + 1) * _s64(int(GOLDEN)))
+
+
+def draw_counts_t(dist: str, h, thresholds: np.ndarray | None = None):
+    import torch
+    hi = _lsr(h, 32)
+    if dist == "bernoulli":
+        c = _lsr(h, 63)
+    elif dist == "uniform3":
+        c = _lsr(hi * 3, 32)
+    elif dist == "geometric":
+        c = torch.zeros_like(h)
+        alive = torch.ones_like(h, dtype=torch.bool)
+        for s in range(63):
+            bit = (_lsr(h, s) & 1).bool() & alive
+            c += bit.to(h.dtype)
+            alive &= bit
+    elif dist == "poisson":
+        thr = poisson1_thresholds() if thresholds is None else thresholds
+        c = torch.zeros_like(h)
+        for t in thr:
+            c += (hi >= int(t)).to(h.dtype)
+    else:
+        raise ValueError(dist)
+    return c.to(torch.int32)
+
+
+def encode_values_t(v, E: int):
+    """Torch twin of encode_values: int32 [n], int64 [n] or int64 [n, 2]."""
+    import torch
+    if E == 4:
+        return (((v + (1 << 31)) & 0xFFFFFFFF) - (1 << 31)).to(torch.int32)
+    if E == 8:
+        return v.clone()
+    x = (v & 0xFFFF).to(torch.float32).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    y = (_lsr(v, 16) & 0xFFFF).to(torch.float32).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    return torch.stack([v, x | (y << 32)], dim=1)
+
+
+def make_insert_inputs_t(spec: "InsertSpec", device):
+    """(counts int32 [R][L][T], packed values) for spec, drawn on `device`."""
+    import torch
+    R, LT = spec.rounds, spec.L * spec.T
+    r = torch.arange(spec.round0, spec.round0 + R, dtype=torch.int64, device=device)
+    gtid = torch.arange(LT, dtype=torch.int64, device=device)
+    keys = (r[:, None] << 32) | gtid[None, :]
+    counts = draw_counts_t(spec.dist, splitmix_at_t(spec.seed, keys), spec.thresholds)
+    flat = counts.reshape(-1).to(torch.int64)
+    n = int(flat.sum().item())
+    g_rep = torch.repeat_interleave(gtid.repeat(R), flat, output_size=n)
+    r_rep = torch.repeat_interleave(r.repeat_interleave(LT), flat, output_size=n)
+    starts = torch.repeat_interleave(torch.cumsum(flat, 0) - flat, flat, output_size=n)
+    k = torch.arange(n, dtype=torch.int64, device=device) - starts
+    va, vb, vc = (_s64(int(c)) for c in spec.coeffs)
+    v = va * g_rep + vb * r_rep + vc * k
+    return counts.reshape(R, spec.L, spec.T), encode_values_t(v, spec.E)
+
+
+def uniform_indices_t(seed: int, n: int, size: int, device):
+    import torch
+    assert 0 < size < (1 << 32)
+    h = splitmix_at_t(seed, torch.arange(n, dtype=torch.int64, device=device))
+    return _lsr(_lsr(h, 32) * size, 32)
+
+
+def index_keyed_values_t(seed: int, idx, E: int):
+    return encode_values_t(splitmix_at_t(seed, idx), E)

@@ -1,0 +1,44 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point include/gga.h declares (no compute calls here)."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2209_00103_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "gga.h")).read()
+    return sorted(set(re.findall(r"^int\s+(gga_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ["gga_create", "gga_insert", "gga_read", "gga_write", "gga_flatten", "gga_size", "gga_destroy"]:
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(gga_\w+)", out))
+    assert set(declared_symbols()) <= exported
+
+
+def test_binding_names_match_header():
+    from paper_2209_00103_gb300 import gga
+    assert sorted(gga.EXPORTED) == declared_symbols()
+
