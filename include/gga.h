@@ -43,7 +43,8 @@ enum {
   GGA_ERR_OUT_OF_RANGE = 3,    /* (device) read/write index >= size */
   GGA_ERR_DST_TOO_SMALL = 4,   /* (device) flatten destination capacity < size */
   GGA_ERR_CUDA = 5,            /* a CUDA runtime call failed */
-  GGA_ERR_TIMEOUT = 6          /* (device) a bounded wait gave up */
+  GGA_ERR_TIMEOUT = 6,         /* (device) a bounded wait gave up */
+  GGA_ERR_TOO_LARGE = 7        /* gga_insert_noalloc: the call needs more than its fixed scratch */
 };
 
 /* Sweep modes for gga_sweep (Sec. VI-B, rw_g and rw_b). */
@@ -132,6 +133,35 @@ int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* ou
  */
 int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
                const void* values_dev, uint64_t n_values, void* stream);
+
+/*
+ * gga_insert_noalloc -- gga_insert for callers that must not allocate GPU
+ * memory while they run: code that owns a fixed memory budget reserved up
+ * front (for example through a caching allocator that holds the rest of the
+ * device), or latency-critical loops where a cudaMalloc/cudaMallocAsync could
+ * block or fail.  The paper has no counterpart; it is an interface variant.
+ *  Arguments, element order, results and device errors are those of
+ *  gga_insert; the handle is created beforehand with gga_create as usual.
+ *  Scratch: gga_insert keeps its per-call scratch (the look-back state of the
+ *  count scan, the first-value index of every (round, block) run and every
+ *  round's position in each LFVector's batch) in a buffer it grows on
+ *  demand.  This variant instead uses one fixed 32 MiB array compiled into
+ *  the library as a static __device__ variable, so it calls no cudaMalloc,
+ *  cudaFree or allocating library routine.  Every GPU that loads the
+ *  library holds those 32 MiB until the process exits.  A call needs at
+ *  most about 16.5 * rounds * L bytes of it (rounds * L <= ~2 million, e.g.
+ *  512 rounds of 1024 LFVectors use 8.5 MiB); a call that needs more
+ *  returns GGA_ERR_TOO_LARGE and enqueues nothing.
+ *  Set-up: the first call on a device looks the array up there
+ *  (cudaGetSymbolAddress, with that device current); make that first call
+ *  before any stream capture.  The current device must be the handle's.
+ *  Sharing: all calls, on all handles, share the one array and it keeps the
+ *  last call's contents (each call clears the part that must start at
+ *  zero).  Calls that overlap on the GPU -- on different streams, or from
+ *  different threads -- race on it; order them.
+ */
+int gga_insert_noalloc(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
+                       const void* values_dev, uint64_t n_values, void* stream);
 
 /*
  * gga_insert_generated -- the same insertion with counts and values drawn

@@ -107,6 +107,17 @@ int sync_status(gga_array* h, cudaStream_t st, bool clear) {
 
 }  // namespace
 
+namespace gga {
+bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device, int* num_sms) {
+  if (!h) return false;
+  *view = h->view;
+  *ins = h->ins;
+  *device = h->device;
+  *num_sms = h->num_sms;
+  return true;
+}
+}  // namespace gga
+
 extern "C" {
 
 int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* out) {

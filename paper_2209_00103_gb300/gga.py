@@ -23,8 +23,9 @@ GGA_ERR_OUT_OF_RANGE = 3
 GGA_ERR_DST_TOO_SMALL = 4
 GGA_ERR_CUDA = 5
 GGA_ERR_TIMEOUT = 6
+GGA_ERR_TOO_LARGE = 7
 ERROR_NAMES = {0: "OK", 1: "INVALID", 2: "POOL_EXHAUSTED", 3: "OUT_OF_RANGE",
-               4: "DST_TOO_SMALL", 5: "CUDA", 6: "TIMEOUT"}
+               4: "DST_TOO_SMALL", 5: "CUDA", 6: "TIMEOUT", 7: "TOO_LARGE"}
 
 GGA_RW_G = 0
 GGA_RW_B = 1
@@ -32,7 +33,7 @@ DIST = {"bernoulli": 0, "uniform3": 1, "geometric": 2, "poisson": 3}
 MAX_THRESHOLDS = 16
 
 # Every symbol include/gga.h declares.
-EXPORTED = ["gga_create", "gga_insert", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
+EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
             "gga_destroy"]
 
@@ -74,6 +75,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
     sig = {
         "gga_create": [ctypes.POINTER(gga_params), vp, vp, ctypes.POINTER(vp)],
         "gga_insert": [vp, vp, u32, vp, u64, vp],
+        "gga_insert_noalloc": [vp, vp, u32, vp, u64, vp],
         "gga_insert_generated": [vp, ctypes.POINTER(gga_gen_spec), u32, vp],
         "gga_read": [vp, vp, u64, vp, vp],
         "gga_write": [vp, vp, u64, vp, vp],
@@ -149,6 +151,17 @@ def gga_insert(h, counts: torch.Tensor, values: torch.Tensor, stream=None):
     n_values = values.shape[0] if values.numel() else 0
     _check(load_library().gga_insert(h, _dptr(counts), counts.shape[0], _dptr(values) if n_values else None,
                                      n_values, _stream(stream)), "gga_insert")
+
+
+def gga_insert_noalloc(h, counts: torch.Tensor, values: torch.Tensor, stream=None):
+    """gga_insert without allocating: per-call scratch lives in the library's
+    fixed 32 MiB device array (see include/gga.h).  Raises GGAError with
+    GGA_ERR_TOO_LARGE when the call needs more scratch than that."""
+    assert counts.dtype in (torch.int32, torch.uint32) and counts.dim() == 3
+    n_values = values.shape[0] if values.numel() else 0
+    _check(load_library().gga_insert_noalloc(h, _dptr(counts), counts.shape[0],
+                                             _dptr(values) if n_values else None, n_values, _stream(stream)),
+           "gga_insert_noalloc")
 
 
 def make_gen_spec(seed: int, dist: str, coeffs, round0: int = 0, thresholds=None) -> gga_gen_spec:
