@@ -142,8 +142,8 @@ int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
  * block or fail.  The paper has no counterpart; it is an interface variant.
  *  Arguments, element order, results and device errors are those of
  *  gga_insert; the handle is created beforehand with gga_create as usual.
- *  Scratch: gga_insert keeps its per-call scratch (the look-back state of the
- *  count scan, the first-value index of every (round, block) run and every
+ *  Scratch: gga_insert keeps its per-call scratch (the tile totals of the
+ *  count pass, the first-value index of every (round, block) run and every
  *  round's position in each LFVector's batch) in a buffer it grows on
  *  demand.  This variant instead uses one fixed 32 MiB array compiled into
  *  the library as a static __device__ variable, so it calls no cudaMalloc,
@@ -156,9 +156,9 @@ int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
  *  (cudaGetSymbolAddress, with that device current); make that first call
  *  before any stream capture.  The current device must be the handle's.
  *  Sharing: all calls, on all handles, share the one array and it keeps the
- *  last call's contents (each call clears the part that must start at
- *  zero).  Calls that overlap on the GPU -- on different streams, or from
- *  different threads -- race on it; order them.
+ *  last call's contents (a call writes every part of it before reading it).
+ *  Calls that overlap on the GPU -- on different streams, or from different
+ *  threads -- race on it; order them.
  */
 int gga_insert_noalloc(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
                        const void* values_dev, uint64_t n_values, void* stream);

@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) read_kernel(ArrayView v, const uint64_t* 
   extern __shared__ uint64_t s_off[];
   const uint64_t* off = stage_offsets(v, s_off);
   const uint64_t N = off[v.L];
-  constexpr int U = 4;
+  constexpr int U = 8;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   bool bad = false;
   for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n; i0 += stride * U) {
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) write_kernel(ArrayView v, const uint64_t*
   extern __shared__ uint64_t s_off[];
   const uint64_t* off = stage_offsets(v, s_off);
   const uint64_t N = off[v.L];
-  constexpr int U = 4;
+  constexpr int U = 8;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
   bool bad = false;
   for (uint64_t i0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i0 < n; i0 += stride * U) {
@@ -126,26 +126,44 @@ __device__ __forceinline__ typename Elem<E>::T add_rep(typename Elem<E>::T x, ui
   return x;
 }
 
-// rw_g: one thread per element, each through the global translation.
+// rw_g: elements are visited by global index, one thread per element, each
+// through the global translation (LFVector by the prefix sum of sizes, then
+// bucket and offset).  A warp takes 32*U consecutive indices; lane 0's
+// binary search is shared by the lanes whose index falls in the same
+// LFVector, the others search for themselves.
 template <int E>
 __global__ void __launch_bounds__(256) sweep_g_kernel(ArrayView v, uint64_t delta, uint32_t repeats) {
   typedef typename Elem<E>::T T;
+  constexpr int U = 8;
   extern __shared__ uint64_t s_off[];
   const uint64_t* off = stage_offsets(v, s_off);
   const uint64_t N = off[v.L];
-  constexpr int U = 4;
-  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
-  for (uint64_t g0 = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x; g0 < N; g0 += stride * U) {
-    Located loc[U];
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
+  for (uint64_t wbase = (static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * U;
+       wbase < N; wbase += warps * 32 * U) {
+    uint32_t l0 = 0;
+    if (lane == 0) l0 = upper_bound_u64(off, v.L + 1, wbase) - 1;
+    l0 = __shfl_sync(0xffffffffu, l0, 0);
+    const uint64_t lo = off[l0], hi = off[l0 + 1];
+    T* addr[U];
     T x[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      loc[u] = locate(v, off, N, g0 + u * stride);
-      if (loc[u].ok) x[u] = *reinterpret_cast<const T*>(loc[u].addr);
+      const uint64_t g = wbase + lane + 32 * u;
+      addr[u] = nullptr;
+      if (g < N) {
+        const uint32_t l = (g >= lo && g < hi) ? l0 : upper_bound_u64(off, v.L + 1, g) - 1;
+        uint32_t b;
+        uint64_t o;
+        bucket_of(g - off[l], v.log2B, b, o);
+        addr[u] = reinterpret_cast<T*>(__ldg(v.buckets + static_cast<uint64_t>(l) * kMaxBuckets + b)) + o;
+        x[u] = *addr[u];
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (loc[u].ok) *reinterpret_cast<T*>(loc[u].addr) = add_rep<E>(x[u], delta, repeats);
+      if (addr[u]) *addr[u] = add_rep<E>(x[u], delta, repeats);
   }
 }
 
@@ -367,15 +385,18 @@ __global__ void __launch_bounds__(kFlThreads) flatten_kernel(ArrayView v, uint8_
 // ---------------------------------------------------------------------------
 // Clear, capacities, accounting.
 
+// Every bucket (live or spare) goes back to the queue of its index.
 __global__ void clear_kernel(ArrayView v) {
   const uint64_t gt = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const uint64_t l = gt / kMaxBuckets;
   const uint32_t b = static_cast<uint32_t>(gt % kMaxBuckets);
   if (l >= v.L) return;
-  const uint32_t nb = v.nbuckets[l];
   uint64_t* slot = v.buckets + l * kMaxBuckets + b;
-  if (b < nb && *slot) pool_free(v.pool, *slot, bucket_len(b, v.log2B) * v.E, v.status);
-  *slot = 0;
+  const uint64_t a = *slot;
+  if (a) {
+    ring_push(v.pool, b, a);
+    *slot = 0;
+  }
 }
 
 __global__ void clear_sizes_kernel(ArrayView v) {
@@ -417,45 +438,67 @@ static size_t offsets_smem(const ArrayView& v) {
   return v.L + 1 <= kSmemOffsetsMax ? (v.L + 1) * sizeof(uint64_t) : 0;
 }
 
-static unsigned grid_for(uint64_t n, int num_sms, int per_sm) {
-  const uint64_t want = (n + 255) / 256;
-  const uint64_t cap = static_cast<uint64_t>(num_sms) * per_sm;
-  return static_cast<unsigned>(want < 1 ? 1 : (want < cap ? want : cap));
+// Grid of one full wave: the blocks that fit on all SMs at once (grid-stride
+// kernels then give every block the same share), but no more than the work.
+template <typename K>
+static unsigned wave_grid(K kern, int threads, size_t smem, int num_sms, uint64_t work_blocks) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const uint64_t wave = static_cast<uint64_t>(num_sms) * per_sm;
+  return static_cast<unsigned>(work_blocks < 1 ? 1 : (work_blocks < wave ? work_blocks : wave));
+}
+
+template <int E>
+static void read_as(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st) {
+  typedef typename Elem<E>::T T;
+  const size_t sm = offsets_smem(v);
+  const unsigned grid = wave_grid(read_kernel<E>, 256, sm, num_sms, (n + 255) / 256);
+  read_kernel<E><<<grid, 256, sm, st>>>(v, idx, n, static_cast<T*>(out));
+}
+
+template <int E>
+static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms,
+                     cudaStream_t st) {
+  typedef typename Elem<E>::T T;
+  const size_t sm = offsets_smem(v);
+  const unsigned grid = wave_grid(write_kernel<E>, 256, sm, num_sms, (n + 255) / 256);
+  write_kernel<E><<<grid, 256, sm, st>>>(v, idx, n, static_cast<const T*>(in));
 }
 
 int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st) {
   if (n == 0) return GGA_OK;
-  const unsigned grid = grid_for(n, num_sms, 8);
-  const size_t sm = offsets_smem(v);
-  if (v.E == 4) read_kernel<4><<<grid, 256, sm, st>>>(v, idx, n, static_cast<uint32_t*>(out));
-  else if (v.E == 8) read_kernel<8><<<grid, 256, sm, st>>>(v, idx, n, static_cast<unsigned long long*>(out));
-  else read_kernel<16><<<grid, 256, sm, st>>>(v, idx, n, static_cast<uint4*>(out));
+  if (v.E == 4) read_as<4>(v, idx, n, out, num_sms, st);
+  else if (v.E == 8) read_as<8>(v, idx, n, out, num_sms, st);
+  else read_as<16>(v, idx, n, out, num_sms, st);
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }
 
 int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms,
                  cudaStream_t st) {
   if (n == 0) return GGA_OK;
-  const unsigned grid = grid_for(n, num_sms, 8);
-  const size_t sm = offsets_smem(v);
-  if (v.E == 4) write_kernel<4><<<grid, 256, sm, st>>>(v, idx, n, static_cast<const uint32_t*>(in));
-  else if (v.E == 8)
-    write_kernel<8><<<grid, 256, sm, st>>>(v, idx, n, static_cast<const unsigned long long*>(in));
-  else write_kernel<16><<<grid, 256, sm, st>>>(v, idx, n, static_cast<const uint4*>(in));
+  if (v.E == 4) write_as<4>(v, idx, n, in, num_sms, st);
+  else if (v.E == 8) write_as<8>(v, idx, n, in, num_sms, st);
+  else write_as<16>(v, idx, n, in, num_sms, st);
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }
 
-int launch_sweep(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms, cudaStream_t st) {
+template <int E>
+static void sweep_as(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms,
+                     cudaStream_t st) {
   if (mode == GGA_RW_G) {
-    const unsigned grid = static_cast<unsigned>(num_sms) * 8;
     const size_t sm = offsets_smem(v);
-    if (v.E == 4) sweep_g_kernel<4><<<grid, 256, sm, st>>>(v, delta, repeats);
-    else sweep_g_kernel<8><<<grid, 256, sm, st>>>(v, delta, repeats);
+    const unsigned grid = wave_grid(sweep_g_kernel<E>, 256, sm, num_sms, ~0ull);
+    sweep_g_kernel<E><<<grid, 256, sm, st>>>(v, delta, repeats);
   } else {
-    const unsigned grid = static_cast<unsigned>(num_sms) * 8;
-    if (v.E == 4) sweep_b_kernel<4><<<grid, 256, 0, st>>>(v, delta, repeats);
-    else sweep_b_kernel<8><<<grid, 256, 0, st>>>(v, delta, repeats);
+    const unsigned grid = wave_grid(sweep_b_kernel<E>, 256, 0, num_sms, ~0ull);
+    sweep_b_kernel<E><<<grid, 256, 0, st>>>(v, delta, repeats);
   }
+}
+
+int launch_sweep(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms, cudaStream_t st) {
+  if (v.E == 4) sweep_as<4>(v, mode, delta, repeats, num_sms, st);
+  else sweep_as<8>(v, mode, delta, repeats, num_sms, st);
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }
 

@@ -50,9 +50,7 @@ bool valid_params(const gga_params* p) {
 }
 
 // Per-call scratch of gga_insert, laid out for up to R_cap rounds:
-// [look-back tile state | voff [rows+1] | pre [L][R+1]].  The tile state
-// sits first so that every call finds its (zeroed) part at the same place:
-// it is zeroed when the buffer is made and each insertion zeroes what it used.
+// [tile prefixes [tiles+1] | row prefixes [rows+1] | pre [L][R+1]].
 uint64_t max_tiles(uint32_t L, uint32_t T, uint32_t R) {
   const uint64_t rows = static_cast<uint64_t>(R) * L;
   const uint64_t a = gga::count_tiles(rows, T, false), b = gga::count_tiles(rows, T, true);
@@ -70,9 +68,9 @@ size_t insert_scratch_bytes(uint32_t L, uint32_t T, uint32_t R) {
 void bind_scratch(gga_array* h, uint32_t R_cap, uint32_t R) {
   const uint32_t L = h->p.n_lfvectors;
   char* c = static_cast<char*>(h->scratch);
-  h->ins.tile_state = reinterpret_cast<unsigned long long*>(c);
+  h->ins.tile_pre = reinterpret_cast<uint64_t*>(c);
   c += align_up(max_tiles(L, h->p.threads_per_block, R_cap) * 8 + 8, 256);
-  h->ins.voff = reinterpret_cast<uint64_t*>(c);
+  h->ins.row_pre = reinterpret_cast<uint64_t*>(c);
   c += align_up((static_cast<uint64_t>(R) * L + 1) * 8, 256);
   h->ins.pre = reinterpret_cast<uint64_t*>(c);
 }
@@ -146,7 +144,7 @@ int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* ou
   const size_t o_sizes = take(L * 8), o_offsets = take((L + 1) * 8), o_buckets = take(L * gga::kMaxBuckets * 8),
                o_nb = take(L * 4), o_fl = take((L + 1) * 8), o_ib = take(L * 8), o_il = take(L * 8),
                o_cp = take((L + 1) * 8), o_pool = take(sizeof(gga::PoolState)), o_status = take(4),
-               o_counters = take(16), o_mem = take(16);
+               o_counters = take(16), o_mem = take(16), o_rings = take(L * gga::kMaxBuckets * 8);
   h->meta_bytes = off;
   if (cudaMalloc(&h->meta, h->meta_bytes) != cudaSuccess) {
     delete h;
@@ -185,6 +183,8 @@ int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* ou
   ps.bump = 0;
   ps.cap = p->pool_bytes;
   ps.base = reinterpret_cast<unsigned long long>(h->slab);
+  ps.rings = reinterpret_cast<unsigned long long>(m + o_rings);
+  ps.ring_cap = L;
   int rc = GGA_OK;
   if (cudaMemsetAsync(h->meta, 0, h->meta_bytes, st) != cudaSuccess ||
       cudaMemcpyAsync(v.pool, &ps, sizeof(ps), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -292,8 +292,13 @@ int gga_memory(gga_handle h, gga_mem* out, void* stream) {
   out->bucket_bytes = ms[0];
   out->live_bytes = ms[1];
   out->pool_bytes = h->p.pool_bytes;
-  out->pool_bump_bytes = ps.bump;
-  out->free_list_bytes = ps.free_bytes;
+  out->pool_bump_bytes = ps.bump < ps.cap ? ps.bump : ps.cap;
+  uint64_t fb = 0;
+  for (int b = 0; b < gga::kMaxBuckets; ++b) {
+    const uint64_t bytes = gga::alloc_bytes_for(gga::bucket_len(b, h->log2B) * h->p.elem_bytes);
+    if (h->log2B + b < 64) fb += (ps.ring_tail[b] - ps.ring_head[b]) * bytes;
+  }
+  out->free_list_bytes = fb;
   out->metadata_bytes = h->meta_bytes;
   return GGA_OK;
 }

@@ -26,12 +26,23 @@ constexpr uint32_t kCasLimit = 1u << 20;     // bound on lock-free retry loops
 constexpr uint32_t kSpinLimit = 1u << 22;    // bound on spin waits (~0.5 s with backoff)
 constexpr uint32_t kChunkBytes = 16384;      // flatten / rw_b work unit
 
+// Device pool (Algorithm 2's malloc, without the host).  Buckets are carved
+// from one slab by a bump pointer; buckets handed back by gga_clear wait in
+// one ring queue per bucket index b (all of size B * 2^b * E) and are reused
+// first.  Queues are touched with atomicAdd only: insertion kernels pop
+// (ring_taken), gga_clear pushes (ring_tail), never both in one kernel, and
+// the single-threaded fix-up after each insertion folds the pops into
+// ring_head.  A handle's LFVectors hold at most one bucket of each index, so
+// a queue never holds more than L entries.
 struct PoolState {
-  unsigned long long bump;                      // slab bytes handed out so far
+  unsigned long long bump;                      // slab bytes handed out (passes cap once exhausted)
   unsigned long long cap;                       // slab bytes
   unsigned long long base;                      // slab address
-  unsigned long long free_head[kPoolClasses];   // (unit + 1) | tag << 40, unit = 256 B
-  unsigned long long free_bytes;                // bytes parked on the free lists
+  unsigned long long ring_head[kMaxBuckets];    // first queued entry
+  unsigned long long ring_tail[kMaxBuckets];    // one past the last queued entry
+  unsigned long long ring_taken[kMaxBuckets];   // pops by the running insertion kernel
+  unsigned long long rings;                     // address of [kMaxBuckets][ring_cap] bucket addresses
+  unsigned long long ring_cap;
 };
 
 struct ArrayView {
@@ -114,73 +125,68 @@ __device__ __forceinline__ V warp_incl_scan(V v) {
 }
 
 // ---------------------------------------------------------------------------
-// Device pool (Algorithm 2's malloc): bump pointer over the slab, plus one
-// intrusive free list per power-of-two size class.  A free bucket stores the
-// next free unit in its first 8 bytes.  Pops happen only in insertion
-// kernels and pushes only in gga_clear, never in the same kernel, so the
-// Treiber stacks see no ABA; the tag is kept anyway.
+// Device pool operations.
 
-__device__ __forceinline__ uint64_t alloc_bytes_for(uint64_t bytes) {
+__host__ __device__ __forceinline__ uint64_t alloc_bytes_for(uint64_t bytes) {
   return bytes < kGrain ? kGrain : bytes;   // bucket sizes are powers of two
 }
 
-__device__ inline uint64_t pool_alloc(PoolState* p, uint64_t bytes, uint32_t* status) {
-  bytes = alloc_bytes_for(bytes);
-  const int cls = 63 - __clzll(static_cast<long long>(bytes));
-  unsigned long long head = *reinterpret_cast<volatile unsigned long long*>(&p->free_head[cls]);
-  for (uint32_t it = 0; it < kCasLimit; ++it) {
-    const uint64_t unit = head & kUnitMask;
-    if (unit == 0) break;
-    const uint64_t addr = p->base + (unit - 1) * kGrain;
-    const uint64_t next = *reinterpret_cast<volatile unsigned long long*>(addr) & kUnitMask;
-    const unsigned long long nh = next | (((head >> 40) + 1) << 40);
-    const unsigned long long prev = atomicCAS(&p->free_head[cls], head, nh);
-    if (prev == head) {
-      atomicAdd(&p->free_bytes, static_cast<unsigned long long>(0ull - bytes));
-      return addr;
-    }
-    head = prev;
-  }
-  unsigned long long cur = *reinterpret_cast<volatile unsigned long long*>(&p->bump);
-  for (uint32_t it = 0; it < kCasLimit; ++it) {
-    if (cur + bytes > p->cap) return 0;
-    const unsigned long long prev = atomicCAS(&p->bump, cur, cur + bytes);
-    if (prev == cur) return p->base + cur;
-    cur = prev;
-  }
-  latch_error(status, GGA_ERR_TIMEOUT);
-  return 0;
+// Pop a queued bucket of index b, or 0 if the queue ran dry.
+__device__ __forceinline__ uint64_t ring_pop(PoolState* p, uint32_t b) {
+  const unsigned long long i = atomicAdd(&p->ring_taken[b], 1ull);
+  const unsigned long long pos = p->ring_head[b] + i;
+  if (pos >= p->ring_tail[b]) return 0;
+  return reinterpret_cast<const uint64_t*>(p->rings)[static_cast<uint64_t>(b) * p->ring_cap + pos % p->ring_cap];
 }
 
-__device__ inline void pool_free(PoolState* p, uint64_t addr, uint64_t bytes, uint32_t* status) {
-  bytes = alloc_bytes_for(bytes);
-  const int cls = 63 - __clzll(static_cast<long long>(bytes));
-  const uint64_t unit = (addr - p->base) / kGrain + 1;
-  unsigned long long head = *reinterpret_cast<volatile unsigned long long*>(&p->free_head[cls]);
-  for (uint32_t it = 0; it < kCasLimit; ++it) {
-    *reinterpret_cast<volatile unsigned long long*>(addr) = head & kUnitMask;
-    __threadfence();
-    const unsigned long long nh = unit | (((head >> 40) + 1) << 40);
-    const unsigned long long prev = atomicCAS(&p->free_head[cls], head, nh);
-    if (prev == head) {
-      atomicAdd(&p->free_bytes, static_cast<unsigned long long>(bytes));
-      return;
-    }
-    head = prev;
-  }
-  latch_error(status, GGA_ERR_TIMEOUT);
+// Queue a bucket of index b (gga_clear only).
+__device__ __forceinline__ void ring_push(PoolState* p, uint32_t b, uint64_t addr) {
+  const unsigned long long j = atomicAdd(&p->ring_tail[b], 1ull);
+  reinterpret_cast<uint64_t*>(p->rings)[static_cast<uint64_t>(b) * p->ring_cap + j % p->ring_cap] = addr;
 }
 
-// Allocate buckets nb..need-1 of LFVector l.  Returns the number of buckets
-// allocated afterwards (== need on success).
+// After an insertion kernel: fold its pops into the queue heads (one thread).
+__device__ __forceinline__ void ring_fixup(PoolState* p) {
+  for (int b = 0; b < kMaxBuckets; ++b) {
+    const unsigned long long h = p->ring_head[b] + p->ring_taken[b];
+    p->ring_head[b] = h < p->ring_tail[b] ? h : p->ring_tail[b];
+    p->ring_taken[b] = 0;
+  }
+}
+
+// Allocate buckets nb..need-1 of LFVector l (Algorithm 2 for every bucket a
+// reservation reaches).  Queued buckets first; the rest with one bump of the
+// slab for all of them.  A bucket index that cannot be served ends the
+// allocated prefix; buckets obtained beyond it stay in the table as spares
+// for the next growth.  Returns the new length of the allocated prefix.
 __device__ inline uint32_t grow_buckets(const ArrayView& v, uint32_t l, uint32_t nb, uint32_t need) {
+  uint64_t* tab = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
+  if (need > static_cast<uint32_t>(kMaxBuckets)) need = kMaxBuckets;
+  uint64_t miss = 0, bump_bytes = 0;
   for (uint32_t b = nb; b < need; ++b) {
-    if (b >= static_cast<uint32_t>(kMaxBuckets)) return b;
-    const uint64_t addr = pool_alloc(v.pool, bucket_len(b, v.log2B) * v.E, v.status);
-    if (addr == 0) return b;
-    v.buckets[static_cast<uint64_t>(l) * kMaxBuckets + b] = addr;
+    if (tab[b] != 0) continue;
+    const uint64_t a = ring_pop(v.pool, b);
+    if (a) {
+      tab[b] = a;
+    } else {
+      miss |= 1ull << b;
+      bump_bytes += alloc_bytes_for(bucket_len(b, v.log2B) * v.E);
+    }
   }
-  return need;
+  if (bump_bytes) {
+    uint64_t off = atomicAdd(&v.pool->bump, static_cast<unsigned long long>(bump_bytes));
+    const uint64_t cap = v.pool->cap, base = v.pool->base;
+    for (uint32_t b = nb; b < need; ++b) {
+      if (!((miss >> b) & 1ull)) continue;
+      const uint64_t sz = alloc_bytes_for(bucket_len(b, v.log2B) * v.E);
+      if (off + sz > cap) break;
+      tab[b] = base + off;
+      off += sz;
+    }
+  }
+  uint32_t got = nb;
+  while (got < need && tab[got] != 0) ++got;
+  return got;
 }
 
 // Chunks of kChunkBytes covering the live part of LFVector of `size`
@@ -241,6 +247,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Raise the transaction count a phase waits for, without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Plain arrival (release at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Global -> shared bulk copy completing on an mbarrier.  16-byte aligned
 // addresses, size a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
@@ -285,13 +302,13 @@ union Vec16 {
 // Host-side launchers (defined in the .cu files).
 
 struct InsertScratch {
-  uint64_t* voff;                 // [n_rows + 1] value offset of every (round, block) run
+  uint64_t* row_pre;              // [n_rows] run's first-value index inside its count tile
   uint64_t* pre;                  // [L][R + 1] run start of every round, relative to the batch base
-  unsigned long long* tile_state; // [n_tiles] decoupled look-back state
+  uint64_t* tile_pre;             // [n_tiles + 1] tile totals, then their exclusive prefix
   uint64_t* ins_base;             // [L] LFVector size before the batch
   uint64_t* ins_len;              // [L] committed elements of the batch
   uint64_t* cp_prefix;            // [L+1] prefix of copy chunks
-  uint32_t* counters;             // [0] tile ticket, [1] done counter
+  uint32_t* counters;             // [1] last-block-done counter of reserve
 };
 
 int launch_insert(const ArrayView& v, const InsertScratch& s, const uint32_t* counts, uint32_t rounds,

@@ -57,7 +57,7 @@ extern "C" int gga_insert_noalloc(gga_handle h, const uint32_t* counts_dev, uint
   if ((reinterpret_cast<uintptr_t>(values_dev) % v.E) != 0 && n_values > 0) return GGA_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(counts_dev) & 3) != 0) return GGA_ERR_INVALID;
 
-  // Scratch layout for this call: [scan state | run offsets | round positions].
+  // Scratch layout for this call: [tile prefixes | row prefixes | round positions].
   const uint64_t rows = static_cast<uint64_t>(rounds) * v.L;
   const bool vec_ok = (reinterpret_cast<uintptr_t>(counts_dev) & 15) == 0;
   const uint64_t tiles = gga::count_tiles(rows, v.T, vec_ok);
@@ -71,13 +71,12 @@ extern "C" int gga_insert_noalloc(gga_handle h, const uint32_t* counts_dev, uint
   if (dev != hdev) return GGA_ERR_INVALID;
   char* base = static_cast<char*>(scratch_on_device(dev));
   if (!base) return GGA_ERR_CUDA;
-  s.tile_state = reinterpret_cast<unsigned long long*>(base);
-  s.voff = reinterpret_cast<uint64_t*>(base + b_tiles);
+  s.tile_pre = reinterpret_cast<uint64_t*>(base);
+  s.row_pre = reinterpret_cast<uint64_t*>(base + b_tiles);
   s.pre = reinterpret_cast<uint64_t*>(base + b_tiles + b_voff);
 
+  // The array keeps whatever the previous call (on any handle) left there;
+  // every part of it this call reads is written by this call's kernels first.
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // The look-back scan state must start at zero; the array keeps whatever
-  // the previous call (on any handle) left there.
-  if (cudaMemsetAsync(s.tile_state, 0, tiles * 8, st) != cudaSuccess) return GGA_ERR_CUDA;
   return gga::launch_insert(v, s, counts_dev, rounds, values_dev, n_values, num_sms, st);
 }
