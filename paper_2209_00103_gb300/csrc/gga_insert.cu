@@ -796,7 +796,8 @@ __device__ __forceinline__ uint32_t gen_count(const GenParams& g, uint64_t h) {
     default: {
       const uint32_t u = static_cast<uint32_t>(h >> 32);
       uint32_t c = 0;
-      for (uint32_t k = 0; k < g.nthr; ++k) c += u >= g.thr[k];
+#pragma unroll
+      for (uint32_t k = 0; k < GGA_MAX_THRESHOLDS; ++k) c += (k < g.nthr) & (u >= g.thr[k]);
       return c;
     }
   }
@@ -819,23 +820,40 @@ constexpr uint32_t kGenStageBytes = 65536;
 
 template <int E> struct GenK { static constexpr int value = E == 16 ? 4 : 8; };
 
+// Warp inclusive scan of two 16-bit counters packed in one word.  Counts per
+// thread are below 64, so a warp sums below 2^11 and a block of <= 1024
+// threads below 2^16: no carry crosses the halves.
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
 // One block per LFVector.  Per pass of K rounds: every thread draws its K
-// counts, a warp-shuffle scan plus one shared-memory pass over the warp
-// totals gives its positions, thread 0 reserves the pass's run and allocates
-// the buckets it reaches, then (synchronize) every thread writes its values
-// at its prefix-sum positions into a shared-memory stage and the block
-// streams the stage to the buckets with aligned 128-bit stores.  A pass that
-// does not fit the stage writes straight to the buckets instead.
+// counts (two rounds per 32-bit word), a warp-shuffle scan plus one
+// shared-memory pass over the warp totals gives every (round, thread) its
+// position (Sec. III-B), thread 0 reserves the pass's run with one size
+// update and allocates the buckets it reaches (Algorithms 1-2), then
+// (synchronize) every thread writes its values at its positions into a
+// shared-memory stage, and the block streams the stage to the buckets with
+// aligned 128-bit stores.  A pass that does not fit the stage writes straight
+// to the buckets instead.
 template <int E, int K>
 __global__ void __launch_bounds__(1024) gen_insert_kernel(ArrayView v, GenParams g, uint32_t R) {
   typedef typename Elem<E>::T T;
   constexpr uint32_t VEC = 16 / E;
   constexpr uint32_t CAP = kGenStageBytes / E;
+  constexpr int KP = K / 2;   // packed words per thread
   extern __shared__ uint4 s_stage4[];
   T* s_stage = reinterpret_cast<T*>(s_stage4);
-  __shared__ uint64_t s_wtot[K][32];
-  __shared__ uint64_t s_rbase[K + 1];
-  __shared__ uint64_t s_base, s_commit;
+  __shared__ uint32_t s_wt[KP][32];      // packed warp prefixes
+  __shared__ uint32_t s_rb[K + 1];       // pass-relative start of every round
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_commit, s_nb;
   __shared__ int s_stop;
 
   const uint32_t l = blockIdx.x, t = threadIdx.x, NT = blockDim.x;
@@ -843,50 +861,64 @@ __global__ void __launch_bounds__(1024) gen_insert_kernel(ArrayView v, GenParams
   const uint64_t gtid = static_cast<uint64_t>(l) * v.T + t;
   const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
   const bool group_ok = v.B >= VEC;
+  const bool active = t < v.T;
   if (t == 0) {
     s_base = v.sizes[l];
+    s_nb = v.nbuckets[l];
     s_stop = 0;
   }
   __syncthreads();
 
   for (uint32_t r0 = 0; r0 < R; r0 += K) {
     const uint32_t kk = min(static_cast<uint32_t>(K), R - r0);
-    uint64_t inc[K];
-    uint32_t cnt[K];
+    uint32_t pk[KP], inc[KP];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
-      cnt[k] = (t < v.T && static_cast<uint32_t>(k) < kk) ? gen_count(g, splitmix(g.seed, (r << 32) | gtid)) : 0u;
-      inc[k] = warp_incl_scan(static_cast<uint64_t>(cnt[k]));
-      if (lane == 31) s_wtot[k][warp] = inc[k];
+    for (int j = 0; j < KP; ++j) {
+      uint32_t c[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = 2 * j + h;
+        const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
+        c[h] = (active && k < kk) ? gen_count(g, splitmix(g.seed, (r << 32) | gtid)) : 0u;
+      }
+      pk[j] = c[0] | (c[1] << 16);
+      inc[j] = warp_incl_scan_u32(pk[j]);
+      if (lane == 31) s_wt[j][warp] = inc[j];
     }
     __syncthreads();
     if (warp == 0) {
-      uint64_t rb = 0;
-      for (int k = 0; k < K; ++k) {
-        const uint64_t w = lane < nwarps ? s_wtot[k][lane] : 0;
-        const uint64_t wi = warp_incl_scan(w);
-        if (lane < nwarps) s_wtot[k][lane] = rb + wi - w;   // pass-relative start of the warp's run
-        if (lane == 0) s_rbase[k] = rb;
-        rb += __shfl_sync(0xffffffffu, wi, 31);
+      uint32_t rb = 0;
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        const uint32_t w = lane < nwarps ? s_wt[j][lane] : 0u;
+        const uint32_t wi = warp_incl_scan_u32(w);
+        if (lane < nwarps) s_wt[j][lane] = wi - w;
+        const uint32_t tot = __shfl_sync(0xffffffffu, wi, 31);
+        if (lane == 0) {
+          s_rb[2 * j] = rb;
+          rb += tot & 0xFFFFu;
+          s_rb[2 * j + 1] = rb;
+          rb += tot >> 16;
+        }
       }
       if (lane == 0) {
-        s_rbase[K] = rb;
+        s_rb[K] = rb;
         // Leader: one size reservation for the pass, then Algorithm 2 for
         // every bucket the run reaches.
         const uint64_t base = s_base;
-        uint64_t commit = rb;
+        uint32_t commit = rb;
         if (rb > 0) {
-          const uint32_t nb = v.nbuckets[l];
+          const uint32_t nb = s_nb;
           const uint32_t need = buckets_for(base + rb, v.log2B);
           if (need > nb) {
             const uint32_t got = grow_buckets(v, l, nb, need);
+            s_nb = got;
             v.nbuckets[l] = got;
             if (got < need) {
               const uint64_t cap = bucket_first(got, v.log2B);
               int kf = 0;
-              while (kf < K && base + s_rbase[kf + 1] <= cap) ++kf;
-              commit = s_rbase[kf];
+              while (kf < K && base + s_rb[kf + 1] <= cap) ++kf;
+              commit = s_rb[kf];
               s_stop = 1;
               latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
             }
@@ -898,48 +930,55 @@ __global__ void __launch_bounds__(1024) gen_insert_kernel(ArrayView v, GenParams
     }
     __syncthreads();   // synchronize(): the buckets exist before any write
 
-    const uint64_t base = s_base, commit = s_commit;
-    const bool staged = commit <= CAP;
+    const uint64_t base = s_base;
+    const uint32_t commit = s_commit;
+    const uint32_t sh = static_cast<uint32_t>(base & (VEC - 1));   // stage index = pass position + sh
+    const bool staged = commit + sh <= CAP;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const uint64_t start = s_wtot[k][warp] + inc[k] - cnt[k];   // this thread's position in the pass
-      const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
-      for (uint32_t j = 0; j < cnt[k]; ++j) {
-        const uint64_t q = start + j;
-        if (q >= commit) break;
-        const T x = gen_value<E>(g.va * gtid + g.vb * r + g.vc * j);
-        if (staged) {
-          s_stage[q] = x;
-        } else {
-          uint32_t bb;
-          uint64_t off;
-          bucket_of(base + q, v.log2B, bb, off);
-          store_elem<E>(bk[bb] + off * E, x);
+    for (int j = 0; j < KP; ++j) {
+      const uint32_t ex = s_wt[j][warp] + inc[j] - pk[j];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = 2 * j + h;
+        const uint32_t c = (pk[j] >> (16 * h)) & 0xFFFFu;
+        if (c == 0) continue;
+        const uint32_t st = s_rb[k] + ((ex >> (16 * h)) & 0xFFFFu);
+        uint64_t val = g.va * gtid + g.vb * (static_cast<uint64_t>(g.round0) + r0 + k);
+        for (uint32_t m = 0; m < c; ++m, val += g.vc) {
+          const uint32_t q = st + m;
+          if (q >= commit) break;
+          if (staged) {
+            s_stage[q + sh] = gen_value<E>(val);
+          } else {
+            uint32_t bb;
+            uint64_t off;
+            bucket_of(base + q, v.log2B, bb, off);
+            store_elem<E>(bk[bb] + off * E, gen_value<E>(val));
+          }
         }
       }
     }
     __syncthreads();
-    if (staged) {
-      const uint64_t gbeg = base & ~static_cast<uint64_t>(VEC - 1);
-      const uint64_t end = base + commit;
-      for (uint64_t p = gbeg + static_cast<uint64_t>(t) * VEC; p < end; p += static_cast<uint64_t>(NT) * VEC) {
-        if (group_ok && p >= base && p + VEC <= end) {
-          Vec16<E> x;
-#pragma unroll
-          for (uint32_t e = 0; e < VEC; ++e) x.e[e] = s_stage[p - base + e];
+    if (staged && commit) {
+      const uint64_t gbeg = base - sh;
+      const uint32_t nvec = (commit + sh + VEC - 1) / VEC;
+      for (uint32_t vi = t; vi < nvec; vi += NT) {
+        const uint64_t p = gbeg + static_cast<uint64_t>(vi) * VEC;
+        const uint32_t lo = vi * VEC;   // stage index of p
+        if (group_ok && lo >= sh && lo + VEC <= commit + sh) {
           uint32_t bb;
           uint64_t off;
           bucket_of(p, v.log2B, bb, off);
-          __stcs(reinterpret_cast<uint4*>(bk[bb] + off * E), x.v);
+          __stcs(reinterpret_cast<uint4*>(bk[bb] + off * E), s_stage4[vi]);
         } else {
 #pragma unroll
           for (uint32_t e = 0; e < VEC; ++e) {
-            const uint64_t pe = p + e;
-            if (pe < base || pe >= end) continue;
+            const uint32_t si = lo + e;
+            if (si < sh || si >= commit + sh) continue;
             uint32_t bb;
             uint64_t off;
-            bucket_of(pe, v.log2B, bb, off);
-            store_elem<E>(bk[bb] + off * E, s_stage[pe - base]);
+            bucket_of(p + e, v.log2B, bb, off);
+            store_elem<E>(bk[bb] + off * E, s_stage[si]);
           }
         }
       }
