@@ -230,6 +230,33 @@ int gga_memory(gga_handle h, gga_mem* out, void* stream);
 /* gga_last_error -- synchronize, return the latched device error and clear it. */
 int gga_last_error(gga_handle h, void* stream);
 
+/*
+ * gga_twophase_spawn -- one spawning generation of the two-phase case study
+ * (Sec. VI-D: an insertion phase grows the array from inside the
+ * application kernel, then the data is flattened for a regular work phase).
+ * Elements are 16-byte records {uint64 id, float pos, float vel} (E must be
+ * 16).  Every parent record of LFVector l spawns Geometric(1/2) - 1 children
+ * into l: the count of the parent at local index j is the number of trailing
+ * one bits of SplitMix64 output ((gen << 48) | (offsets[l] + j)) + 1 of the
+ * stream seeded with `seed` (offsets as when the call starts); children are
+ * appended in parent order, a parent's children consecutively, and copy the
+ * parent's pos and vel with id = ((gen + 1) << 56) | (l << 40) | (local index
+ * of the child).  Parents are all records present when the call starts
+ * (only_newborn = 0), or for only_newborn = 1 the records from born_dev[l]
+ * (uint64 [L], device, updated to the size at the start of the call).
+ * Device errors as gga_insert (pool exhausted: the LFVector keeps the passes
+ * that fit).
+ */
+int gga_twophase_spawn(gga_handle h, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born_dev,
+                       void* stream);
+
+/*
+ * gga_twophase_work -- the case study's work phase on a flattened array of n
+ * records (16-byte aligned device pointer): `passes` streaming passes, each
+ * adding vel to pos of every record (one round-to-nearest float add).
+ */
+int gga_twophase_work(void* records_dev, uint64_t n, uint32_t passes, void* stream);
+
 /* gga_destroy -- free the handle's metadata and its own slab (a borrowed slab
  * is left to its owner).  Synchronizes the device first. */
 int gga_destroy(gga_handle h);

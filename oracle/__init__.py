@@ -85,6 +85,9 @@ def _load():
         lib.orc_bucket_bytes.argtypes = [ctypes.c_void_p]
         lib.orc_splitmix_at.restype = ctypes.c_uint64
         lib.orc_splitmix_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_spawn.restype = ctypes.c_int
+        lib.orc_spawn.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, u8p]
+        lib.orc_work_passes.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint32]
         lib.orc_draw_count.restype = ctypes.c_uint32
         lib.orc_draw_count.argtypes = [ctypes.c_uint32, ctypes.c_uint64, u8p, ctypes.c_uint32]
         _lib = lib
@@ -204,6 +207,13 @@ class OracleGGArray:
         self._lib.orc_lfvector(self._h, l, _ptr(out))
         return out[:n]
 
+    def spawn(self, gen: int, seed: int, only_newborn: bool = False, born: np.ndarray | None = None):
+        """Spawning generation of the two-phase case study (see orc_spawn)."""
+        if only_newborn:
+            assert born is not None and born.dtype == np.uint64 and born.shape == (self.L,)
+        self._check(self._lib.orc_spawn(self._h, gen, seed & 0xFFFFFFFFFFFFFFFF, int(only_newborn),
+                                        _ptr(born) if only_newborn else None), "spawn")
+
     def bucket_bytes(self) -> int:
         return int(self._lib.orc_bucket_bytes(self._h))
 
@@ -222,6 +232,13 @@ def capacity_of(size: int, B: int) -> int:
 
 def splitmix_at(seed: int, key: int) -> int:
     return int(_load().orc_splitmix_at(seed & 0xFFFFFFFFFFFFFFFF, key & 0xFFFFFFFFFFFFFFFF))
+
+
+def work_passes(records: np.ndarray, passes: int) -> np.ndarray:
+    """pos += vel, `passes` times, on flattened 16-byte records (in place)."""
+    assert records.dtype.itemsize == 16 and records.flags["C_CONTIGUOUS"]
+    _load().orc_work_passes(_ptr(records), records.shape[0], passes)
+    return records
 
 
 def draw_count(dist: str, h: int, thresholds: np.ndarray | None = None) -> int:

@@ -395,6 +395,62 @@ uint64_t orc_bucket_bytes(void* h) {
   return bytes;
 }
 
+// ---------------------------------------------------------------------------
+// Two-phase case study (Sec. VI-D): an insertion phase that grows the array
+// from inside the kernel, then flatten, then regular passes over the static
+// copy.  Records are 16 bytes {uint64 id, float pos, float vel}.
+
+// Spawning generation `gen`: every parent record of LFVector l appends
+// Geometric(1/2) - 1 children to the same LFVector (the push_back of
+// Algorithm 1 called from inside the application kernel).  The count of the
+// parent at LFVector-local index j is the trailing-ones count of
+// splitmix_at(seed, (gen << 48) | g) with g = offsets[l] + j, the parent's
+// global index when the generation starts.  Children are appended in parent
+// order, a parent's children consecutively; a child copies its parent's pos
+// and vel and gets id ((gen + 1) << 56) | (l << 40) | (its local index).
+// Parents are all records present when the generation starts
+// (only_newborn = 0), or only those appended by the previous generation
+// (only_newborn = 1, born[l] holds where they start and is advanced).
+int orc_spawn(void* h, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born) {
+  OracleArray& a = *static_cast<OracleArray*>(h);
+  if (a.E != 16) return ORC_ERR_INVALID;
+  std::vector<uint64_t> off = prefix_offsets(a);
+  for (uint32_t l = 0; l < a.L; ++l) {
+    const uint64_t s = lfv_size(a, l);
+    const uint64_t first = only_newborn ? born[l] : 0;
+    for (uint64_t j = first; j < s; ++j) {
+      const uint64_t key = (static_cast<uint64_t>(gen) << 48) | (off[l] + j);
+      const uint32_t c = draw_count(2, splitmix_at(seed, key), nullptr, 0);
+      unsigned char parent[16];
+      std::memcpy(parent, a.lfv[l].data() + j * 16, 16);
+      for (uint32_t k = 0; k < c; ++k) {
+        const uint64_t local = lfv_size(a, l);
+        const uint64_t id = (static_cast<uint64_t>(gen + 1) << 56) | (static_cast<uint64_t>(l) << 40) | local;
+        std::memcpy(parent, &id, 8);
+        a.lfv[l].insert(a.lfv[l].end(), parent, parent + 16);
+      }
+    }
+    if (only_newborn) born[l] = s;
+  }
+  return ORC_OK;
+}
+
+// Work phase of the case study on the flattened records: pos += vel,
+// `passes` times, one float addition each (Sec. VI-D's kernel "adds 1 to
+// every element", here with a per-record increment).
+void orc_work_passes(void* records, uint64_t n, uint32_t passes) {
+  unsigned char* r = static_cast<unsigned char*>(records);
+  for (uint32_t p = 0; p < passes; ++p) {
+    for (uint64_t i = 0; i < n; ++i) {
+      float pos, vel;
+      std::memcpy(&pos, r + i * 16 + 8, 4);
+      std::memcpy(&vel, r + i * 16 + 12, 4);
+      pos = pos + vel;
+      std::memcpy(r + i * 16 + 8, &pos, 4);
+    }
+  }
+}
+
 // The n-th draw of the counter-based generator and a count drawn from it,
 // exposed so tests can compare this C implementation with other ones.
 uint64_t orc_splitmix_at(uint64_t seed, uint64_t key) { return splitmix_at(seed, key); }

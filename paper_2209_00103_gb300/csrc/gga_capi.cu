@@ -308,6 +308,22 @@ int gga_last_error(gga_handle h, void* stream) {
   return sync_status(h, S(stream), true);
 }
 
+int gga_twophase_spawn(gga_handle h, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born_dev,
+                       void* stream) {
+  if (!h || h->p.elem_bytes != 16 || (only_newborn && !born_dev)) return GGA_ERR_INVALID;
+  if (born_dev && (reinterpret_cast<uintptr_t>(born_dev) & 7) != 0) return GGA_ERR_INVALID;
+  return gga::launch_twophase_spawn(h->view, gen, seed, only_newborn ? 1 : 0, born_dev, S(stream));
+}
+
+int gga_twophase_work(void* records_dev, uint64_t n, uint32_t passes, void* stream) {
+  if (n > 0 && (!records_dev || (reinterpret_cast<uintptr_t>(records_dev) & 15) != 0)) return GGA_ERR_INVALID;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return GGA_ERR_CUDA;
+  return gga::launch_twophase_work(records_dev, n, passes, sms, S(stream));
+}
+
 int gga_destroy(gga_handle h) {
   if (!h) return GGA_ERR_INVALID;
   int rc = GGA_OK;

@@ -325,6 +325,10 @@ int launch_clear(const ArrayView& v, cudaStream_t st);
 int launch_caps(const ArrayView& v, uint64_t* caps, cudaStream_t st);
 int launch_memory(const ArrayView& v, uint64_t* out2, cudaStream_t st);
 
+int launch_twophase_spawn(const ArrayView& v, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born,
+                          cudaStream_t st);
+int launch_twophase_work(void* records, uint64_t n, uint32_t passes, int num_sms, cudaStream_t st);
+
 // Handle internals for entry points defined outside gga_capi.cu.
 bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device, int* num_sms);
 uint64_t count_tiles(uint64_t n_rows, uint32_t T, bool vec_ok);

@@ -35,7 +35,7 @@ MAX_THRESHOLDS = 16
 # Every symbol include/gga.h declares.
 EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
-            "gga_destroy"]
+            "gga_destroy", "gga_twophase_spawn", "gga_twophase_work"]
 
 
 class gga_params(ctypes.Structure):
@@ -87,6 +87,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_memory": [vp, ctypes.POINTER(gga_mem), vp],
         "gga_last_error": [vp, vp],
         "gga_destroy": [vp],
+        "gga_twophase_spawn": [vp, u32, u64, i32, vp, vp],
+        "gga_twophase_work": [vp, u64, u32, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +235,20 @@ def gga_last_error(h, stream=None) -> int:
 
 def gga_destroy(h):
     _check(load_library().gga_destroy(h), "gga_destroy")
+
+
+def gga_twophase_spawn(h, gen: int, seed: int, born: torch.Tensor | None = None, stream=None):
+    """One spawning generation of the two-phase case study (all records spawn
+    unless `born` (int64 [L], device) is given: then only those from born[l])."""
+    _check(load_library().gga_twophase_spawn(h, gen, seed & 0xFFFFFFFFFFFFFFFF, 0 if born is None else 1,
+                                             _dptr(born) if born is not None else None, _stream(stream)),
+           "gga_twophase_spawn")
+
+
+def gga_twophase_work(records: torch.Tensor, passes: int, stream=None):
+    """pos += vel, `passes` streaming passes over flattened records ([n, 2] int64)."""
+    _check(load_library().gga_twophase_work(_dptr(records), records.shape[0], passes, _stream(stream)),
+           "gga_twophase_work")
 
 
 # ---------------------------------------------------------------------------

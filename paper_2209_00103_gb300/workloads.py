@@ -311,3 +311,65 @@ def uniform_indices_t(seed: int, n: int, size: int, device):
 
 def index_keyed_values_t(seed: int, idx, E: int):
     return encode_values_t(splitmix_at_t(seed, idx), E)
+
+
+# ---------------------------------------------------------------------------
+# Two-phase case study (Sec. VI-D): initial 16-byte records, spawned
+# generations, then flatten and streaming passes.
+
+RECORD_DTYPE = np.dtype([("id", "<u8"), ("pos", "<f4"), ("vel", "<f4")])
+
+
+def initial_records(n0: int) -> np.ndarray:
+    """Record i = {id i, pos (i & 1023), vel ((7 i) & 15) / 16}: dyadic values,
+    so 20 additions of vel stay exact in float32."""
+    i = np.arange(n0, dtype=np.uint64)
+    r = np.zeros(n0, dtype=RECORD_DTYPE)
+    r["id"] = i
+    r["pos"] = (i & np.uint64(1023)).astype(np.float32)
+    r["vel"] = ((i * np.uint64(7)) & np.uint64(15)).astype(np.float32) / np.float32(16)
+    return r
+
+
+def initial_records_t(n0: int, device):
+    """Torch twin of initial_records as int64 [n0, 2] (id, pos|vel bits)."""
+    import torch
+    i = torch.arange(n0, dtype=torch.int64, device=device)
+    pos = (i & 1023).to(torch.float32).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    vel = (((i * 7) & 15).to(torch.float32) / 16).view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    return torch.stack([i, pos | (vel << 32)], dim=1)
+
+
+def split_counts(L: int, T: int, n0: int) -> np.ndarray:
+    """One insertion round placing records [l*n0/L, (l+1)*n0/L) in LFVector l,
+    spread over its T threads as evenly as possible: counts [1][L][T]."""
+    per_l = np.diff((np.arange(L + 1, dtype=np.int64) * n0) // L)
+    c = np.zeros((1, L, T), dtype=np.uint32)
+    t = np.arange(T + 1, dtype=np.int64)
+    for l in range(L):
+        c[0, l] = np.diff((t * int(per_l[l])) // T)
+    return c
+
+
+@dataclass
+class TwoPhaseWorkload:
+    name: str
+    L: int
+    T: int
+    B: int
+    n0: int
+    generations: int
+    seed: int
+    passes: int
+    only_newborn: bool
+
+
+def two_phase(only_newborn: bool = False, n0: int = 1 << 24, generations: int = 8) -> TwoPhaseWorkload:
+    """2^24 initial records over 1024 LFVectors x 512 threads, 8 generations
+    of Geometric(1/2)-1 children per record (mean 1), then flatten and 20
+    passes of pos += vel.  only_newborn=False: every record present spawns
+    (the population about doubles per generation); True: only the previous
+    generation's children spawn."""
+    tag = "newborn" if only_newborn else "all"
+    return TwoPhaseWorkload(f"two_phase_{tag}_1024x512_B4096_n{n0}_g{generations}", 1024, 512, 4096, n0,
+                            generations, 5, 20, only_newborn)

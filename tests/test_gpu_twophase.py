@@ -1,0 +1,99 @@
+"""GPU parity of the two-phase case study (Sec. VI-D): spawning generations
+pushed back from inside the application kernel, flatten, then streaming
+passes of pos += vel over the contiguous copy -- bit for bit against the
+oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_00103_gb300 import gga
+from paper_2209_00103_gb300 import workloads as wl
+
+from harness import assert_same_state, counts_to_dev, dev_to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def grow(L, T, B, n0, generations, only_newborn, seed=5, pool_bytes=None, check_each=True):
+    counts = wl.split_counts(L, T, n0)
+    recs = wl.initial_records(n0)
+    if pool_bytes is None:
+        pool_bytes = 64 * n0 * 16 * (4 if not only_newborn else 1) + L * B * 16 * 8 + (64 << 20)
+    g = gga.GGArray(L, T, B, 16, pool_bytes)
+    o = oracle.OracleGGArray(L, T, B, 16)
+    g.insert(counts_to_dev(counts), torch.from_numpy(recs.view(np.int64).reshape(-1, 2)).cuda())
+    o.insert(counts, recs.view(np.dtype((np.void, 16))))
+    born_d = torch.zeros(L, dtype=torch.int64, device="cuda")
+    born_o = np.zeros(L, dtype=np.uint64)
+    for gen in range(generations):
+        gga.gga_twophase_spawn(g.h, gen, seed, born_d if only_newborn else None)
+        o.spawn(gen, seed, only_newborn, born_o)
+        if check_each:
+            assert_same_state(g, o)
+            if only_newborn:
+                assert np.array_equal(born_d.cpu().numpy().astype(np.uint64), born_o)
+    return g, o
+
+
+def work_phase_matches(g, o, passes):
+    n, rc = g.size()
+    assert rc == gga.GGA_OK
+    flat = g.flatten()
+    gga.gga_twophase_work(flat, passes)
+    want = oracle.work_passes(o.flatten().copy(), passes)
+    assert dev_to_np(flat, 16)[:n].tobytes() == want.tobytes()
+
+
+@pytest.mark.parametrize("only_newborn", [False, True])
+@pytest.mark.parametrize("L,T,B,n0", [(1, 32, 1, 100), (7, 96, 4, 5000), (3, 1000, 16, 20011)])
+def test_spawn_small_shapes(L, T, B, n0, only_newborn):
+    g, o = grow(L, T, B, n0, 5, only_newborn)
+    work_phase_matches(g, o, 20)
+    g.close()
+
+
+def test_spawn_all_records_medium():
+    # Every record spawns: 2^18 initial records, 8 generations (~2^26 records).
+    g, o = grow(64, 512, 256, 1 << 18, 8, False, pool_bytes=4 << 30, check_each=False)
+    assert_same_state(g, o)
+    assert o.size() > (1 << 25)
+    work_phase_matches(g, o, 20)
+    g.close()
+
+
+def test_two_phase_newborn_full_size():
+    # The case-study workload with 2^24 initial records over 1024 LFVectors x
+    # 512 threads, B = 4096, 8 generations where the newborns spawn.
+    w = wl.two_phase(only_newborn=True)
+    g, o = grow(w.L, w.T, w.B, w.n0, w.generations, True, seed=w.seed,
+                pool_bytes=6 << 30, check_each=False)
+    assert_same_state(g, o)
+    work_phase_matches(g, o, w.passes)
+    g.close()
+
+
+def test_spawn_pool_exhaustion_keeps_prefix():
+    L, T, B, n0 = 4, 64, 64, 4000
+    counts = wl.split_counts(L, T, n0)
+    recs = wl.initial_records(n0)
+    g = gga.GGArray(L, T, B, 16, 600 * 1024)
+    g.insert(counts_to_dev(counts), torch.from_numpy(recs.view(np.int64).reshape(-1, 2)).cuda())
+    n0_, rc = g.size()
+    assert rc == gga.GGA_OK and n0_ == n0
+    for gen in range(6):
+        gga.gga_twophase_spawn(g.h, gen, 5)
+    n, rc, sizes, caps = g.sizes_caps()
+    assert rc == gga.GGA_ERR_POOL_EXHAUSTED
+    assert bool((sizes <= caps).all())
+    flat = dev_to_np(g.flatten(), 16)[:n].view(wl.RECORD_DTYPE)
+    # Every record is self-describing: generation 0 records are the initial
+    # ones, spawned records carry their own LFVector-local index.
+    off = g.offsets().cpu().numpy()
+    gen = (flat["id"] >> np.uint64(56)).astype(np.int64)
+    kids = np.nonzero(gen > 0)[0]
+    loc = flat["id"][kids] & np.uint64((1 << 40) - 1)
+    lv = ((flat["id"][kids] >> np.uint64(40)) & np.uint64(0xFFFF)).astype(np.int64)
+    assert np.array_equal(off[lv].astype(np.uint64) + loc, kids.astype(np.uint64))
+    g.close()

@@ -319,3 +319,75 @@ def test_tiny_workload_self_describing_values():
     for l in range(w.L):
         seg = gtid[off[l]:off[l + 1]] // w.T
         assert np.all(seg == l)
+
+
+# --------------------------------------------------------------------------
+# Two-phase case study: spawning generations against an independent numpy
+# model (np.repeat of parents by their drawn counts), and the work phase
+# against its closed form.
+
+def spawn_model(lfvs, gen, seed, only_newborn, born):
+    sizes = np.array([len(x) for x in lfvs], dtype=np.uint64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    out = []
+    for l, rec in enumerate(lfvs):
+        s = len(rec)
+        first = int(born[l]) if only_newborn else 0
+        j = np.arange(first, s, dtype=np.uint64)
+        keys = (np.uint64(gen) << np.uint64(48)) | (off[l] + j)
+        c = wl.draw_counts("geometric", wl.splitmix_at(seed, keys))
+        kids = np.repeat(rec[first:s], c.astype(np.int64))
+        local = np.uint64(s) + np.arange(len(kids), dtype=np.uint64)
+        kids["id"] = (np.uint64(gen + 1) << np.uint64(56)) | (np.uint64(l) << np.uint64(40)) | local
+        out.append(np.concatenate([rec, kids]))
+        if only_newborn:
+            born[l] = s
+    return out
+
+
+@pytest.mark.parametrize("only_newborn", [False, True])
+def test_spawn_matches_repeat_model(only_newborn):
+    L, T, B, n0 = 5, 8, 4, 300
+    counts = wl.split_counts(L, T, n0)
+    recs = wl.initial_records(n0)
+    a = oracle.OracleGGArray(L, T, B, 16)
+    a.insert(counts, recs.view(np.dtype((np.void, 16))))
+    per_l = counts.sum(axis=2)[0]
+    bounds = np.concatenate([[0], np.cumsum(per_l)]).astype(np.int64)
+    lfvs = [recs[bounds[l]:bounds[l + 1]].copy() for l in range(L)]
+    born_o = np.zeros(L, dtype=np.uint64)
+    born_m = np.zeros(L, dtype=np.uint64)
+    for gen in range(5):
+        a.spawn(gen, 5, only_newborn, born_o)
+        lfvs = spawn_model(lfvs, gen, 5, only_newborn, born_m)
+        assert np.array_equal(born_o, born_m)
+        for l in range(L):
+            assert a.lfvector(l).tobytes() == lfvs[l].tobytes(), (gen, l)
+    # Children carry their parents' pos/vel and self-describing ids.
+    flat = a.flatten().view(wl.RECORD_DTYPE)
+    gen_of = (flat["id"] >> np.uint64(56)).astype(np.int64)
+    assert gen_of.max() >= 3
+    kids = flat[gen_of > 0]
+    loc = kids["id"] & np.uint64((1 << 40) - 1)
+    lv = (kids["id"] >> np.uint64(40)) & np.uint64(0xFFFF)
+    off = a.offsets()
+    glob = off[lv.astype(np.int64)] + loc
+    assert np.array_equal(np.sort(glob), np.nonzero(gen_of > 0)[0].astype(np.uint64))
+
+
+def test_work_passes_closed_form():
+    r = wl.initial_records(5000)
+    want = r["pos"].astype(np.float64) + 20 * r["vel"].astype(np.float64)
+    got = oracle.work_passes(r.view(np.dtype((np.void, 16))).copy(), 20).view(wl.RECORD_DTYPE)
+    assert np.array_equal(got["pos"].astype(np.float64), want)      # dyadic: exact
+    assert np.array_equal(got["vel"], r["vel"]) and np.array_equal(got["id"], r["id"])
+
+
+def test_split_counts_and_initial_records():
+    c = wl.split_counts(7, 5, 1000)
+    assert c.sum() == 1000
+    per_l = c.sum(axis=2)[0]
+    assert per_l.max() - per_l.min() <= 1
+    r = wl.initial_records(2048)
+    assert r["pos"][1024] == 0 and r["pos"][1023] == 1023
+    assert r["vel"][1] == 7 / 16 and r["vel"][3] == 5 / 16
