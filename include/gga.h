@@ -65,6 +65,7 @@ enum {
 #define GGA_MAX_THRESHOLDS 16
 
 typedef struct gga_array* gga_handle;
+typedef struct gga_pool_t* gga_pool;
 
 typedef struct {
   uint32_t n_lfvectors;        /* L >= 1: LFVectors = thread blocks */
@@ -101,6 +102,39 @@ typedef struct {
   uint64_t free_list_bytes;  /* bytes parked on the per-size free lists */
   uint64_t metadata_bytes;   /* descriptors, offsets, bucket tables, work lists */
 } gga_mem;
+
+/*
+ * gga_pool_create -- a bucket pool several GGArrays can share (Algorithm 2's
+ * malloc done on the device: a bump pointer over one slab plus one free
+ * queue per power-of-two bucket size; buckets handed back are reused first).
+ *  pool_bytes       : slab size.
+ *  slab_dev         : device slab of pool_bytes bytes, 256-byte aligned,
+ *                     borrowed (must outlive the pool); NULL = allocate one.
+ *  min_bucket_bytes : smallest bucket (B * E) any array in the pool will
+ *                     use; the queues take pool_bytes / min_bucket_bytes * 16
+ *                     bytes of device memory at most.
+ * Arrays made with gga_create_in_pool allocate from it.  All calls on arrays
+ * of one pool must be ordered on the device (one stream, or events):
+ * allocation and release are not safe to overlap.
+ */
+int gga_pool_create(uint64_t pool_bytes, void* slab_dev, uint64_t min_bucket_bytes, void* stream, gga_pool* out);
+
+/* gga_pool_destroy -- free the pool (its arrays must be destroyed first).
+ * Synchronizes the device. */
+int gga_pool_destroy(gga_pool pool);
+
+/* gga_pool_info -- out4 (host) = {slab bytes, slab bytes handed out by the
+ * bump pointer, bytes waiting in the free queues, bytes of queue storage}.
+ * Synchronizes. */
+int gga_pool_info(gga_pool pool, uint64_t* out4, void* stream);
+
+/*
+ * gga_create_in_pool -- like gga_create, but buckets come from a shared
+ * pool (p->pool_bytes is ignored).  GGA_ERR_INVALID if B * E is smaller than
+ * the pool's min_bucket_bytes.  gga_destroy returns the array's buckets to
+ * the pool.
+ */
+int gga_create_in_pool(const gga_params* p, gga_pool pool, void* stream, gga_handle* out);
 
 /*
  * gga_create -- make an empty GGArray (Sec. IV).
@@ -257,8 +291,53 @@ int gga_twophase_spawn(gga_handle h, uint32_t gen, uint64_t seed, int only_newbo
  */
 int gga_twophase_work(void* records_dev, uint64_t n, uint32_t passes, void* stream);
 
-/* gga_destroy -- free the handle's metadata and its own slab (a borrowed slab
- * is left to its owner).  Synchronizes the device first. */
+/*
+ * Batched growth: many arrays grown in one persistent launch.
+ *
+ * A job names an array, the draws of its counts and values (the spec of
+ * gga_insert_generated) and a target size.  LFVector l of the array targets
+ * target / L elements, plus one for the first target % L LFVectors.  It runs
+ * rounds r = spec.round0, round0 + 1, ... while below its target: every
+ * thread draws its count for the round, and a thread's elements past the
+ * target are not inserted (the block scan clips them), so the LFVector
+ * holds the prefix of its draw sequence up to the target.  Arrays may have
+ * different T (<= 1024), B, E and pools.
+ */
+typedef struct gga_batch_t* gga_batch;
+
+typedef struct {
+  gga_handle array;
+  gga_gen_spec spec;
+  uint64_t target;
+} gga_batch_job;
+
+/* gga_batch_create -- build the batch's device tables (allocates; jobs is a
+ * host array read during the call; the arrays must outlive the batch). */
+int gga_batch_create(const gga_batch_job* jobs, uint32_t n_jobs, void* stream, gga_batch* out);
+
+/* gga_batch_grow -- grow every job's array to its target: one persistent
+ * kernel over all (array, LFVector) items, one kernel for the pools, one to
+ * finalize the arrays.  Allocates nothing, does not synchronize.  Device
+ * errors are latched in each array (pool exhausted: the LFVector keeps the
+ * rounds that fit). */
+int gga_batch_grow(gga_batch b, void* stream);
+
+/* gga_batch_clear -- empty every array of the batch (buckets back to their
+ * pools) in two kernels. */
+int gga_batch_clear(gga_batch b, void* stream);
+
+/* gga_batch_capture -- capture clear + grow on `stream` (not the legacy
+ * default stream) into a CUDA graph kept by the batch; gga_batch_replay
+ * launches it. */
+int gga_batch_capture(gga_batch b, void* stream);
+int gga_batch_replay(gga_batch b, void* stream);
+
+/* gga_batch_destroy -- free the batch's tables (not its arrays). */
+int gga_batch_destroy(gga_batch b);
+
+/* gga_destroy -- free the handle's metadata and its private pool (a borrowed
+ * slab is left to its owner); an array of a shared pool first returns its
+ * buckets to the pool.  Synchronizes the device. */
 int gga_destroy(gga_handle h);
 
 #ifdef __cplusplus

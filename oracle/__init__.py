@@ -85,6 +85,10 @@ def _load():
         lib.orc_bucket_bytes.argtypes = [ctypes.c_void_p]
         lib.orc_splitmix_at.restype = ctypes.c_uint64
         lib.orc_splitmix_at.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_grow_to_target.restype = ctypes.c_int
+        lib.orc_grow_to_target.argtypes = [
+            ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, u8p, ctypes.c_uint32, ctypes.c_uint64,
+            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
         lib.orc_spawn.restype = ctypes.c_int
         lib.orc_spawn.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, u8p]
         lib.orc_work_passes.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint32]
@@ -159,6 +163,14 @@ class OracleGGArray:
             va, vb, vc, round0, rounds, _ptr(cnt))
         self._check(rc, "insert_generated")
         return cnt
+
+    def grow_to_target(self, seed: int, dist: str, coeffs, target: int, round0: int = 0,
+                       thresholds: np.ndarray | None = None, max_rounds: int = 1 << 20):
+        thr = None if thresholds is None else np.ascontiguousarray(thresholds, dtype=np.uint32)
+        va, vb, vc = (int(c) & 0xFFFFFFFFFFFFFFFF for c in coeffs)
+        rc = self._lib.orc_grow_to_target(self._h, seed & 0xFFFFFFFFFFFFFFFF, DIST[dist], _ptr(thr),
+                                          0 if thr is None else len(thr), va, vb, vc, round0, target, max_rounds)
+        self._check(rc, "grow_to_target")
 
     def size(self) -> int:
         return int(self._lib.orc_size(self._h))

@@ -266,6 +266,36 @@ int orc_insert_generated(void* h, uint64_t seed, uint32_t dist, const uint32_t* 
   return ORC_OK;
 }
 
+// Growth to a target size (batched arrays): LFVector l's target is
+// target / L plus one for the first target % L LFVectors.  LFVector l runs
+// rounds r = round0, round0 + 1, ... while its size is below its target; in
+// each round its threads t = 0..T-1 draw counts as in orc_insert_generated
+// and push_back in thread order until the target is reached (a thread's
+// elements past the target are not inserted).  Fails if some LFVector has
+// not reached its target after max_rounds rounds.
+int orc_grow_to_target(void* h, uint64_t seed, uint32_t dist, const uint32_t* thr, uint32_t nthr, uint64_t va,
+                       uint64_t vb, uint64_t vc, uint32_t round0, uint64_t target, uint32_t max_rounds) {
+  OracleArray& a = *static_cast<OracleArray*>(h);
+  if (dist > 3 || (dist == 3 && thr == nullptr)) return ORC_ERR_INVALID;
+  std::vector<unsigned char> e(a.E);
+  for (uint32_t l = 0; l < a.L; ++l) {
+    const uint64_t tl = target / a.L + (l < target % a.L ? 1 : 0);
+    uint32_t n = 0;
+    for (uint64_t r = round0; lfv_size(a, l) < tl; ++r, ++n) {
+      if (n >= max_rounds) return ORC_ERR_INVALID;
+      for (uint32_t t = 0; t < a.T && lfv_size(a, l) < tl; ++t) {
+        const uint64_t gtid = static_cast<uint64_t>(l) * a.T + t;
+        const uint32_t c = draw_count(dist, splitmix_at(seed, (r << 32) | gtid), thr, nthr);
+        for (uint32_t k = 0; k < c && lfv_size(a, l) < tl; ++k) {
+          make_value(va * gtid + vb * r + vc * k, a.E, e.data());
+          a.lfv[l].insert(a.lfv[l].end(), e.begin(), e.end());
+        }
+      }
+    }
+  }
+  return ORC_OK;
+}
+
 // Global size (Sec. IV: the GGArray keeps the global size).
 uint64_t orc_size(void* h) {
   OracleArray& a = *static_cast<OracleArray*>(h);

@@ -1,0 +1,152 @@
+"""Batched GGArrays: the workload of thousands of arrays of uneven size grown
+in one persistent launch, the per-array parameter rule, and its autotuner.
+
+Every array a gets: payload size E = (4, 8, 16)[a % 3] bytes, a target
+size S_a = min(16M, floor(exp(ln 65536 + 1.5 z_a))) (at least 1) with z_a a
+standard normal drawn by Box-Muller from the counter-based generator, and
+Poisson(1) per-thread counts per round.  The rule maps S_a to (threads per
+block T, LFVectors L_a, first bucket B); the autotuner measures candidate
+rules on the GPU and keeps the fastest whose memory stays within 2x the
+needed memory plus the first buckets.
+"""
+
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+from dataclasses import asdict, dataclass
+
+import numpy as np
+
+from . import workloads as wl
+
+TUNED_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned_batch.json")
+MAX_SIZE = 16 << 20
+
+
+def batched_sizes(n: int = 4096, seed: int = 3) -> np.ndarray:
+    """Lognormal target sizes (median 64K, sigma 1.5, capped 16M, >= 1)."""
+    h1 = wl.splitmix_at(seed, np.arange(n, dtype=np.uint64) * np.uint64(2))
+    h2 = wl.splitmix_at(seed, np.arange(n, dtype=np.uint64) * np.uint64(2) + np.uint64(1))
+    u1 = ((h1 >> np.uint64(11)).astype(np.float64) + 1.0) / float(1 << 53)   # (0, 1]
+    u2 = (h2 >> np.uint64(11)).astype(np.float64) / float(1 << 53)           # [0, 1)
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+    s = np.floor(np.exp(math.log(65536.0) + 1.5 * z))
+    return np.clip(s, 1, MAX_SIZE).astype(np.int64)
+
+
+def payload_bytes(a: int) -> int:
+    return (4, 8, 16)[a % 3]
+
+
+@dataclass
+class Rule:
+    """Per-array parameters from the target size: L_a = ceil(S / per_lfv)
+    (1..max_l), B = the power of two nearest (S / L_a) / b_div, within
+    [256, 65536]; T fixed."""
+    T: int = 256
+    per_lfv: int = 32768
+    b_div: int = 16
+    max_l: int = 1024
+
+    def params(self, size: int):
+        L = int(min(self.max_l, max(1, -(-int(size) // self.per_lfv))))
+        per = max(1, int(size) // L)
+        b = max(1.0, per / self.b_div)
+        B = int(min(65536, max(256, 1 << int(round(math.log2(b))))))
+        return self.T, L, B
+
+
+def spec_for(gga_mod, a: int):
+    """Counts Poisson(1) and self-describing values for array a."""
+    thr = wl.poisson1_thresholds()
+    return gga_mod.make_gen_spec((3 << 32) | a, "poisson", (0x10001, 0x9E3779B9, 7), round0=0, thresholds=thr)
+
+
+def build(sizes, rule: Rule, stream=None, pool_slack: float = 2.3):
+    """Make the arrays (one shared pool) and the batch; returns
+    (pool, arrays, batch, params list)."""
+    from . import gga
+    params = [rule.params(int(s)) for s in sizes]
+    need = sum(int(s) * payload_bytes(a) for a, s in enumerate(sizes))
+    first = sum(L * B * payload_bytes(a) for a, (_, L, B) in enumerate(params))
+    pool_bytes = int(pool_slack * need + 2 * first + (256 << 20))
+    pool = gga.GGAPool(pool_bytes, 256 * 4, stream=stream)
+    arrays, jobs = [], []
+    for a, (s, (T, L, B)) in enumerate(zip(sizes, params)):
+        g = gga.GGArray(L, T, B, payload_bytes(a), shared_pool=pool, stream=stream)
+        arrays.append(g)
+        jobs.append((g, spec_for(gga, a), int(s)))
+    batch = gga.GGABatch(jobs, stream=stream)
+    return pool, arrays, batch, params
+
+
+def teardown(pool, arrays, batch):
+    batch.close()
+    for g in arrays:
+        g.close()
+    pool.close()
+
+
+def time_batch(batch, stream, steps: int = 5, warmup: int = 2) -> float:
+    """Median milliseconds of one captured clear+grow replay."""
+    import torch
+    batch.capture(stream)
+    for _ in range(warmup):
+        batch.replay(stream)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        batch.replay(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sorted(a.elapsed_time(b) for a, b in evs)[steps // 2]
+
+
+def memory_ratio(arrays) -> float:
+    used = need = 0
+    for g in arrays:
+        m = g.memory()
+        used += m["bucket_bytes"]
+        need += m["live_bytes"]
+    return used / max(1, need)
+
+
+def candidates():
+    for T in (128, 256, 512, 1024):
+        for per_lfv in (8192, 32768, 131072):
+            for b_div in (4, 16):
+                yield Rule(T=T, per_lfv=per_lfv, b_div=b_div)
+
+
+def autotune(sizes, stream, out_path: str = TUNED_FILE, max_ratio: float = 2.05, log=print):
+    """Measure every candidate rule on the GPU; keep the fastest whose memory
+    ratio is at most max_ratio.  Writes the choice and all measurements."""
+    results = []
+    total = int(np.sum(sizes))
+    for rule in candidates():
+        pool, arrays, batch, _ = build(sizes, rule, stream)
+        ms = time_batch(batch, stream)
+        ratio = memory_ratio(arrays)
+        teardown(pool, arrays, batch)
+        rec = {"rule": asdict(rule), "ms": ms, "gelem_s": total / (ms / 1e3) / 1e9, "mem_ratio": ratio}
+        results.append(rec)
+        log(json.dumps(rec))
+    ok = [r for r in results if r["mem_ratio"] <= max_ratio] or results
+    best = min(ok, key=lambda r: r["ms"])
+    doc = {"chosen": best["rule"], "measured": results, "n_arrays": len(sizes), "elements": total,
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
+    with open(out_path, "w") as f:
+        json.dump(doc, f, indent=1)
+    return Rule(**best["rule"])
+
+
+def tuned_rule() -> Rule:
+    """The rule the autotuner chose, or the default rule."""
+    try:
+        with open(TUNED_FILE) as f:
+            return Rule(**json.load(f)["chosen"])
+    except (OSError, KeyError, ValueError, TypeError):
+        return Rule()

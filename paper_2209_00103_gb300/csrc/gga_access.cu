@@ -394,7 +394,7 @@ __global__ void clear_kernel(ArrayView v) {
   uint64_t* slot = v.buckets + l * kMaxBuckets + b;
   const uint64_t a = *slot;
   if (a) {
-    ring_push(v.pool, b, a);
+    if (!ring_push(v.pool, class_of(bucket_len(b, v.log2B) * v.E), a)) latch_error(v.status, GGA_ERR_INVALID);
     *slot = 0;
   }
 }

@@ -1,0 +1,359 @@
+// gga_batch.cu -- many GGArrays grown in one persistent launch.
+//
+// A batch is a list of jobs: an array, the draws of its counts and values
+// (as gga_insert_generated), and a target size.  gga_batch_grow runs one
+// persistent kernel over all (array, LFVector) items, largest first, taken
+// from an atomic ticket: a block grows its LFVector round by round -- every
+// thread draws its count, a block scan gives positions, counts are clipped
+// at the LFVector's target by the same scan, the leader reserves and
+// allocates, the block writes (Algorithm 1 with thread coarsening: a block
+// of 128 threads plays T <= 1024 threads).  Then one kernel folds the pool
+// pops and one finalizes every array.  Nothing allocates and nothing waits
+// on the host, so the whole step can be captured in a CUDA graph and
+// replayed (gga_batch_capture / gga_batch_replay).
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "gga_gen.cuh"
+
+namespace gga {
+
+int launch_clear(const ArrayView& v, cudaStream_t st);
+
+namespace {
+
+constexpr int kBatchThreads = 128;
+constexpr int kBatchMaxK = 8;              // virtual threads per physical thread (T <= 1024)
+constexpr uint32_t kBatchMaxRounds = 1u << 20;
+
+struct BatchJob {
+  ArrayView v;
+  GenParams g;
+  uint64_t target;
+};
+
+struct BatchItem {
+  uint32_t job;
+  uint32_t l;
+};
+
+template <int E>
+__device__ __forceinline__ void put_elem(uint64_t addr, uint64_t val) {
+  typedef typename Elem<E>::T T;
+  *reinterpret_cast<T*>(addr) = gen_value<E>(val);
+}
+
+// Grow LFVector l of job J to its target.  All kBatchThreads threads call it.
+template <int E>
+__device__ void grow_item(const BatchJob& J, uint32_t l, uint32_t* s_wsum, uint64_t* s_state) {
+  const ArrayView& v = J.v;
+  const GenParams& g = J.g;
+  const uint32_t t0 = threadIdx.x, lane = t0 & 31, warp = t0 >> 5;
+  const uint32_t k = (v.T + kBatchThreads - 1) / kBatchThreads;   // virtual threads per thread
+  const uint64_t target = J.target / v.L + (l < J.target % v.L ? 1 : 0);
+  const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
+  if (t0 == 0) {
+    s_state[0] = v.sizes[l];      // size
+    s_state[1] = v.nbuckets[l];   // allocated buckets
+    s_state[2] = 0;               // stop flag
+  }
+  __syncthreads();
+  uint32_t rounds = 0;
+  for (uint64_t r = g.round0;; ++r, ++rounds) {
+    const uint64_t size = s_state[0];
+    if (size >= target || s_state[2]) break;
+    if (rounds >= kBatchMaxRounds) {
+      if (t0 == 0) latch_error(v.status, GGA_ERR_TIMEOUT);
+      break;
+    }
+    // Draw this thread's k virtual counts (virtual thread t = t0 * k + i).
+    uint32_t c[kBatchMaxK];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kBatchMaxK; ++i) {
+      const uint32_t t = t0 * k + i;
+      c[i] = 0;
+      if (static_cast<uint32_t>(i) < k && t < v.T)
+        c[i] = gen_count(g, splitmix(g.seed, (r << 32) | (static_cast<uint64_t>(l) * v.T + t)));
+      sum += c[i];
+    }
+    // Block exclusive scan of the per-thread sums.
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= static_cast<uint32_t>(o)) inc += n;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < kBatchThreads / 32; ++w) {
+      const uint32_t x = s_wsum[w];
+      if (static_cast<uint32_t>(w) < warp) wpre += x;
+      total += x;
+    }
+    const uint64_t rem = target - size;
+    const uint64_t commit = total < rem ? total : rem;   // counts past the target are clipped
+    if (t0 == 0 && commit) {
+      // Leader: reservation and Algorithm 2 for the buckets it reaches.
+      const uint32_t nb = static_cast<uint32_t>(s_state[1]);
+      const uint32_t need = buckets_for(size + commit, v.log2B);
+      if (need > nb) {
+        const uint32_t got = grow_buckets(v, l, nb, need);
+        s_state[1] = got;
+        v.nbuckets[l] = got;
+        if (got < need) {
+          s_state[2] = 1;
+          latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
+        }
+      }
+    }
+    __syncthreads();   // synchronize(): buckets exist before any write
+    if (!s_state[2]) {
+      uint64_t run = wpre + inc - sum;   // this thread's first position in the round
+#pragma unroll
+      for (int i = 0; i < kBatchMaxK; ++i) {
+        const uint32_t t = t0 * k + i;
+        if (c[i] && run < commit) {
+          const uint64_t gtid = static_cast<uint64_t>(l) * v.T + t;
+          const uint64_t take = min(static_cast<uint64_t>(c[i]), commit - run);
+          uint64_t val = g.va * gtid + g.vb * r;
+          for (uint64_t m = 0; m < take; ++m, val += g.vc) {
+            uint32_t bb;
+            uint64_t off;
+            bucket_of(size + run + m, v.log2B, bb, off);
+            put_elem<E>(bk[bb] + off * E, val);
+          }
+        }
+        run += c[i];
+      }
+    }
+    __syncthreads();
+    if (t0 == 0 && !s_state[2]) {
+      s_state[0] = size + commit;
+      v.sizes[l] = size + commit;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads) batch_grow_kernel(const BatchJob* __restrict__ jobs,
+                                                                   const BatchItem* __restrict__ items,
+                                                                   uint32_t n_items, uint32_t* ticket) {
+  __shared__ uint32_t s_wsum[kBatchThreads / 32];
+  __shared__ uint64_t s_state[3];
+  __shared__ uint32_t s_item;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    const BatchJob& J = jobs[item.job];
+    switch (J.v.E) {
+      case 4: grow_item<4>(J, item.l, s_wsum, s_state); break;
+      case 8: grow_item<8>(J, item.l, s_wsum, s_state); break;
+      default: grow_item<16>(J, item.l, s_wsum, s_state); break;
+    }
+  }
+}
+
+// Fold the pops of the grow kernel into every pool's queue heads; reset
+// the ticket for the next run.
+__global__ void batch_fixup_kernel(PoolState* const* pools, uint32_t n_pools, uint32_t* ticket) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_pools) ring_fixup(pools[i]);
+  if (i == 0) *ticket = 0;
+}
+
+__global__ void __launch_bounds__(256) batch_finalize_kernel(const BatchJob* __restrict__ jobs) {
+  __shared__ uint64_t s_warp[33];
+  finalize_block(jobs[blockIdx.x].v, nullptr, nullptr, nullptr, 1, s_warp);
+}
+
+// Every bucket of every item back to its pool's queue; sizes to zero.
+__global__ void batch_clear_kernel(const BatchJob* __restrict__ jobs, const BatchItem* __restrict__ items) {
+  const BatchItem item = items[blockIdx.x];
+  const ArrayView& v = jobs[item.job].v;
+  const uint64_t l = item.l;
+  for (uint32_t b = threadIdx.x; b < static_cast<uint32_t>(kMaxBuckets); b += blockDim.x) {
+    uint64_t* slot = v.buckets + l * kMaxBuckets + b;
+    const uint64_t a = *slot;
+    if (a) {
+      if (!ring_push(v.pool, class_of(bucket_len(b, v.log2B) * v.E), a)) latch_error(v.status, GGA_ERR_INVALID);
+      *slot = 0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    v.sizes[l] = 0;
+    v.nbuckets[l] = 0;
+  }
+}
+
+}  // namespace
+}  // namespace gga
+
+struct gga_batch_t {
+  gga::BatchJob* jobs;
+  gga::BatchItem* items;
+  gga::PoolState** pools;
+  uint32_t* ticket;
+  uint32_t n_jobs, n_items, n_pools;
+  int num_sms;
+  unsigned grid;
+  cudaGraphExec_t graph;
+  bool has_graph;
+};
+
+namespace {
+
+int batch_grow(gga_batch_t* b, cudaStream_t st) {
+  if (b->n_items) {
+    gga::batch_grow_kernel<<<b->grid, gga::kBatchThreads, 0, st>>>(b->jobs, b->items, b->n_items, b->ticket);
+    gga::batch_fixup_kernel<<<(b->n_pools + 63) / 64 + 1, 64, 0, st>>>(b->pools, b->n_pools, b->ticket);
+  }
+  if (b->n_jobs) gga::batch_finalize_kernel<<<b->n_jobs, 256, 0, st>>>(b->jobs);
+  return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
+}
+
+int batch_clear(gga_batch_t* b, cudaStream_t st) {
+  if (b->n_items) gga::batch_clear_kernel<<<b->n_items, 64, 0, st>>>(b->jobs, b->items);
+  if (b->n_jobs) gga::batch_finalize_kernel<<<b->n_jobs, 256, 0, st>>>(b->jobs);
+  return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gga_batch_create(const gga_batch_job* jobs, uint32_t n_jobs, void* stream, gga_batch* out) {
+  if (!out || (n_jobs && !jobs)) return GGA_ERR_INVALID;
+  *out = nullptr;
+  std::vector<gga::BatchJob> hj(n_jobs);
+  std::vector<std::pair<uint64_t, gga::BatchItem>> hi;
+  std::vector<gga::PoolState*> hp;
+  int num_sms = 0;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    gga::InsertScratch ins;
+    int dev = 0;
+    if (!gga::handle_parts(jobs[j].array, &hj[j].v, &ins, &dev, &num_sms)) return GGA_ERR_INVALID;
+    const gga_gen_spec& sp = jobs[j].spec;
+    if (sp.dist > GGA_DIST_POISSON || sp.n_thresholds > GGA_MAX_THRESHOLDS ||
+        (sp.dist == GGA_DIST_POISSON && sp.n_thresholds == 0))
+      return GGA_ERR_INVALID;
+    hj[j].g = gga::make_gen_params(sp);
+    hj[j].target = jobs[j].target;
+    const uint32_t L = hj[j].v.L;
+    for (uint32_t l = 0; l < L; ++l) {
+      const uint64_t tl = jobs[j].target / L + (l < jobs[j].target % L ? 1 : 0);
+      if (tl) hi.push_back({tl, gga::BatchItem{j, l}});
+    }
+    if (std::find(hp.begin(), hp.end(), hj[j].v.pool) == hp.end()) hp.push_back(hj[j].v.pool);
+  }
+  // Largest LFVectors first: the ticket then balances the tail.
+  std::stable_sort(hi.begin(), hi.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<gga::BatchItem> items(hi.size());
+  for (size_t i = 0; i < hi.size(); ++i) items[i] = hi[i].second;
+
+  gga_batch_t* b = new (std::nothrow) gga_batch_t();
+  if (!b) return GGA_ERR_CUDA;
+  b->n_jobs = n_jobs;
+  b->n_items = static_cast<uint32_t>(items.size());
+  b->n_pools = static_cast<uint32_t>(hp.size());
+  b->has_graph = false;
+  b->jobs = nullptr;
+  b->items = nullptr;
+  b->pools = nullptr;
+  b->ticket = nullptr;
+  if (num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  b->num_sms = num_sms;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gga::batch_grow_kernel, gga::kBatchThreads, 0) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  b->grid = static_cast<unsigned>(num_sms * per_sm);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = GGA_OK;
+  if (cudaMalloc(&b->jobs, sizeof(gga::BatchJob) * (n_jobs ? n_jobs : 1)) != cudaSuccess ||
+      cudaMalloc(&b->items, sizeof(gga::BatchItem) * (items.empty() ? 1 : items.size())) != cudaSuccess ||
+      cudaMalloc(&b->pools, sizeof(gga::PoolState*) * (hp.empty() ? 1 : hp.size())) != cudaSuccess ||
+      cudaMalloc(&b->ticket, sizeof(uint32_t)) != cudaSuccess)
+    rc = GGA_ERR_CUDA;
+  if (rc == GGA_OK &&
+      ((n_jobs && cudaMemcpyAsync(b->jobs, hj.data(), sizeof(gga::BatchJob) * n_jobs, cudaMemcpyHostToDevice, st) !=
+                      cudaSuccess) ||
+       (!items.empty() && cudaMemcpyAsync(b->items, items.data(), sizeof(gga::BatchItem) * items.size(),
+                                          cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+       (!hp.empty() && cudaMemcpyAsync(b->pools, hp.data(), sizeof(gga::PoolState*) * hp.size(),
+                                       cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+       cudaMemsetAsync(b->ticket, 0, sizeof(uint32_t), st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = GGA_ERR_CUDA;
+  if (rc != GGA_OK) {
+    gga_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return GGA_OK;
+}
+
+int gga_batch_grow(gga_batch b, void* stream) {
+  if (!b) return GGA_ERR_INVALID;
+  return batch_grow(b, static_cast<cudaStream_t>(stream));
+}
+
+int gga_batch_clear(gga_batch b, void* stream) {
+  if (!b) return GGA_ERR_INVALID;
+  return batch_clear(b, static_cast<cudaStream_t>(stream));
+}
+
+int gga_batch_capture(gga_batch b, void* stream) {
+  if (!b || !stream) return GGA_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->has_graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->has_graph = false;
+  }
+  cudaGraph_t g;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GGA_ERR_CUDA;
+  int rc = batch_clear(b, st);
+  if (rc == GGA_OK) rc = batch_grow(b, st);
+  if (cudaStreamEndCapture(st, &g) != cudaSuccess) return GGA_ERR_CUDA;
+  if (rc != GGA_OK) {
+    cudaGraphDestroy(g);
+    return rc;
+  }
+  const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return GGA_ERR_CUDA;
+  b->has_graph = true;
+  return GGA_OK;
+}
+
+int gga_batch_replay(gga_batch b, void* stream) {
+  if (!b || !b->has_graph) return GGA_ERR_INVALID;
+  return cudaGraphLaunch(b->graph, static_cast<cudaStream_t>(stream)) == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
+}
+
+int gga_batch_destroy(gga_batch b) {
+  if (!b) return GGA_ERR_INVALID;
+  int rc = GGA_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (b->has_graph) cudaGraphExecDestroy(b->graph);
+  if (b->jobs) cudaFree(b->jobs);
+  if (b->items) cudaFree(b->items);
+  if (b->pools) cudaFree(b->pools);
+  if (b->ticket) cudaFree(b->ticket);
+  delete b;
+  return rc;
+}
+
+}  // extern "C"

@@ -16,6 +16,18 @@ namespace gga {
 uint64_t count_tiles(uint64_t n_rows, uint32_t T, bool vec_ok);
 }
 
+// A bucket pool: one slab, its bump pointer and the per-class free queues.
+struct gga_pool_t {
+  gga::PoolState* state;   // device
+  void* slab;
+  bool own_slab;
+  void* rings;             // device, uint64 slots of all classes
+  uint64_t ring_slots;
+  uint64_t bytes;
+  uint64_t min_bucket_bytes;
+  int device;
+};
+
 struct gga_array {
   gga_params p;
   uint32_t log2B;
@@ -23,8 +35,8 @@ struct gga_array {
   int num_sms;
   void* meta;
   size_t meta_bytes;
-  void* slab;
-  bool own_slab;
+  gga_pool_t* pool;
+  bool own_pool;
   void* scratch;
   size_t scratch_bytes;
   uint32_t scratch_rounds;
@@ -92,6 +104,87 @@ int ensure_scratch(gga_array* h, uint32_t R, cudaStream_t st) {
   return GGA_OK;
 }
 
+// Make a pool of `bytes` (slab lent, or allocated when slab == nullptr).
+// Queues exist for the byte classes from that of min_bucket_bytes up; a
+// class's queue holds at most min(bytes >> c, lfv_hint * k) entries, k = 8
+// for the 256-byte class (several small bucket indices share it), 1 above;
+// lfv_hint = 0 means no hint (bounded by the slab only).
+int pool_make(uint64_t bytes, void* slab, uint64_t min_bucket_bytes, uint64_t lfv_hint, cudaStream_t st,
+              gga_pool_t** out) {
+  gga_pool_t* pl = new (std::nothrow) gga_pool_t();
+  if (!pl) return GGA_ERR_CUDA;
+  pl->bytes = bytes;
+  pl->min_bucket_bytes = min_bucket_bytes;
+  pl->own_slab = slab == nullptr;
+  pl->slab = slab;
+  pl->rings = nullptr;
+  pl->state = nullptr;
+  if (cudaGetDevice(&pl->device) != cudaSuccess) {
+    delete pl;
+    return GGA_ERR_CUDA;
+  }
+  gga::PoolState ps;
+  std::memset(&ps, 0, sizeof(ps));
+  uint64_t slots = 0;
+  for (uint32_t c = gga::class_of(min_bucket_bytes ? min_bucket_bytes : 1); c < 64; ++c) {
+    uint64_t n = bytes >> c;
+    if (lfv_hint) {
+      const uint64_t h = lfv_hint * (c == 8 ? 8 : 1);
+      if (h < n) n = h;
+    }
+    ps.ring_off[c] = slots;
+    ps.ring_cap[c] = n;
+    slots += n;
+  }
+  pl->ring_slots = slots;
+  int rc = GGA_OK;
+  if (pl->own_slab && bytes > 0 && cudaMalloc(&pl->slab, bytes) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (rc == GGA_OK && slots && cudaMalloc(&pl->rings, slots * 8) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (rc == GGA_OK && cudaMalloc(reinterpret_cast<void**>(&pl->state), sizeof(gga::PoolState)) != cudaSuccess)
+    rc = GGA_ERR_CUDA;
+  if (rc == GGA_OK) {
+    ps.cap = bytes;
+    ps.base = reinterpret_cast<unsigned long long>(pl->slab);
+    ps.rings = reinterpret_cast<unsigned long long>(pl->rings);
+    if (cudaMemcpyAsync(pl->state, &ps, sizeof(ps), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = GGA_ERR_CUDA;
+  }
+  if (rc != GGA_OK) {
+    if (pl->state) cudaFree(pl->state);
+    if (pl->rings) cudaFree(pl->rings);
+    if (pl->own_slab && pl->slab) cudaFree(pl->slab);
+    delete pl;
+    return rc;
+  }
+  *out = pl;
+  return GGA_OK;
+}
+
+int pool_free(gga_pool_t* pl) {
+  int rc = GGA_OK;
+  if (cudaDeviceSynchronize() != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (pl->state && cudaFree(pl->state) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (pl->rings && cudaFree(pl->rings) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (pl->own_slab && pl->slab && cudaFree(pl->slab) != cudaSuccess) rc = GGA_ERR_CUDA;
+  delete pl;
+  return rc;
+}
+
+// Bytes parked in a pool's queues and its bump high-water mark (synchronizes).
+int pool_read(gga_pool_t* pl, cudaStream_t st, uint64_t* bump, uint64_t* free_bytes) {
+  gga::PoolState ps;
+  if (cudaMemcpyAsync(&ps, pl->state, sizeof(ps), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GGA_ERR_CUDA;
+  *bump = ps.bump < ps.cap ? ps.bump : ps.cap;
+  uint64_t fb = 0;
+  for (int c = 0; c < 64; ++c)
+    if (ps.ring_cap[c]) fb += (ps.ring_tail[c] - ps.ring_head[c]) << c;
+  *free_bytes = fb;
+  return GGA_OK;
+}
+
 int sync_status(gga_array* h, cudaStream_t st, bool clear) {
   uint32_t status = 0;
   if (cudaMemcpyAsync(&status, h->view.status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GGA_ERR_CUDA;
@@ -116,25 +209,21 @@ bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device
 }
 }  // namespace gga
 
-extern "C" {
-
-int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* out) {
-  if (!out || !valid_params(p)) return GGA_ERR_INVALID;
-  if (pool_dev && (reinterpret_cast<uintptr_t>(pool_dev) & (gga::kGrain - 1)) != 0) return GGA_ERR_INVALID;
-  *out = nullptr;
-  cudaStream_t st = S(stream);
+// Metadata and scratch of a handle living in `pool`.
+static int handle_make(const gga_params* p, gga_pool_t* pool, bool own_pool, cudaStream_t st, gga_handle* out) {
   gga_array* h = new (std::nothrow) gga_array();
   if (!h) return GGA_ERR_CUDA;
   h->p = *p;
   h->log2B = 0;
   while ((1ull << h->log2B) < p->base_bucket) ++h->log2B;
+  h->pool = pool;
+  h->own_pool = own_pool;
   if (cudaGetDevice(&h->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
     delete h;
     return GGA_ERR_CUDA;
   }
   const uint64_t L = p->n_lfvectors;
-  // Metadata layout.
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -143,8 +232,7 @@ int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* ou
   };
   const size_t o_sizes = take(L * 8), o_offsets = take((L + 1) * 8), o_buckets = take(L * gga::kMaxBuckets * 8),
                o_nb = take(L * 4), o_fl = take((L + 1) * 8), o_ib = take(L * 8), o_il = take(L * 8),
-               o_cp = take((L + 1) * 8), o_pool = take(sizeof(gga::PoolState)), o_status = take(4),
-               o_counters = take(16), o_mem = take(16), o_rings = take(L * gga::kMaxBuckets * 8);
+               o_cp = take((L + 1) * 8), o_status = take(4), o_counters = take(16), o_mem = take(16);
   h->meta_bytes = off;
   if (cudaMalloc(&h->meta, h->meta_bytes) != cudaSuccess) {
     delete h;
@@ -157,7 +245,7 @@ int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* ou
   v.buckets = reinterpret_cast<uint64_t*>(m + o_buckets);
   v.nbuckets = reinterpret_cast<uint32_t*>(m + o_nb);
   v.fl_prefix = reinterpret_cast<uint64_t*>(m + o_fl);
-  v.pool = reinterpret_cast<gga::PoolState*>(m + o_pool);
+  v.pool = pool->state;
   v.status = reinterpret_cast<uint32_t*>(m + o_status);
   v.B = p->base_bucket;
   v.L = p->n_lfvectors;
@@ -169,37 +257,66 @@ int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* ou
   h->ins.cp_prefix = reinterpret_cast<uint64_t*>(m + o_cp);
   h->ins.counters = reinterpret_cast<uint32_t*>(m + o_counters);
   h->memstats = reinterpret_cast<unsigned long long*>(m + o_mem);
-
-  // Slab.
-  h->own_slab = pool_dev == nullptr;
-  h->slab = pool_dev;
-  if (h->own_slab && p->pool_bytes > 0 && cudaMalloc(&h->slab, p->pool_bytes) != cudaSuccess) {
-    cudaFree(h->meta);
-    delete h;
-    return GGA_ERR_CUDA;
-  }
-  gga::PoolState ps;
-  std::memset(&ps, 0, sizeof(ps));
-  ps.bump = 0;
-  ps.cap = p->pool_bytes;
-  ps.base = reinterpret_cast<unsigned long long>(h->slab);
-  ps.rings = reinterpret_cast<unsigned long long>(m + o_rings);
-  ps.ring_cap = L;
-  int rc = GGA_OK;
-  if (cudaMemsetAsync(h->meta, 0, h->meta_bytes, st) != cudaSuccess ||
-      cudaMemcpyAsync(v.pool, &ps, sizeof(ps), cudaMemcpyHostToDevice, st) != cudaSuccess)
-    rc = GGA_ERR_CUDA;
   h->scratch = nullptr;
   h->scratch_bytes = 0;
   h->scratch_rounds = 0;
+  int rc = cudaMemsetAsync(h->meta, 0, h->meta_bytes, st) == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
   if (rc == GGA_OK) rc = ensure_scratch(h, 64, st);
   if (rc == GGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (rc != GGA_OK) {
+    h->own_pool = false;   // the caller disposes of the pool
     gga_destroy(h);
     return rc;
   }
   *out = h;
   return GGA_OK;
+}
+
+extern "C" {
+
+int gga_pool_create(uint64_t pool_bytes, void* slab_dev, uint64_t min_bucket_bytes, void* stream, gga_pool* out) {
+  if (!out || pool_bytes == 0 || min_bucket_bytes == 0) return GGA_ERR_INVALID;
+  if (slab_dev && (reinterpret_cast<uintptr_t>(slab_dev) & (gga::kGrain - 1)) != 0) return GGA_ERR_INVALID;
+  *out = nullptr;
+  return pool_make(pool_bytes, slab_dev, min_bucket_bytes, 0, S(stream), out);
+}
+
+int gga_pool_destroy(gga_pool pool) {
+  if (!pool) return GGA_ERR_INVALID;
+  return pool_free(pool);
+}
+
+int gga_pool_info(gga_pool pool, uint64_t* out4, void* stream) {
+  if (!pool || !out4) return GGA_ERR_INVALID;
+  uint64_t bump = 0, fb = 0;
+  const int rc = pool_read(pool, S(stream), &bump, &fb);
+  if (rc != GGA_OK) return rc;
+  out4[0] = pool->bytes;
+  out4[1] = bump;
+  out4[2] = fb;
+  out4[3] = pool->ring_slots * 8;
+  return GGA_OK;
+}
+
+int gga_create(const gga_params* p, void* pool_dev, void* stream, gga_handle* out) {
+  if (!out || !valid_params(p)) return GGA_ERR_INVALID;
+  if (pool_dev && (reinterpret_cast<uintptr_t>(pool_dev) & (gga::kGrain - 1)) != 0) return GGA_ERR_INVALID;
+  *out = nullptr;
+  cudaStream_t st = S(stream);
+  gga_pool_t* pool = nullptr;
+  int rc = pool_make(p->pool_bytes, pool_dev, p->base_bucket * p->elem_bytes, p->n_lfvectors, st, &pool);
+  if (rc != GGA_OK) return rc;
+  rc = handle_make(p, pool, true, st, out);
+  if (rc != GGA_OK) pool_free(pool);
+  return rc;
+}
+
+int gga_create_in_pool(const gga_params* p, gga_pool pool, void* stream, gga_handle* out) {
+  if (!out || !pool || !valid_params(p)) return GGA_ERR_INVALID;
+  if (gga::alloc_bytes_for(p->base_bucket * p->elem_bytes) < gga::alloc_bytes_for(pool->min_bucket_bytes))
+    return GGA_ERR_INVALID;   // the pool does not serve this array's smallest bucket
+  *out = nullptr;
+  return handle_make(p, pool, false, S(stream), out);
 }
 
 int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds, const void* values_dev,
@@ -284,22 +401,16 @@ int gga_memory(gga_handle h, gga_mem* out, void* stream) {
   if (cudaMemsetAsync(h->memstats, 0, 16, st) != cudaSuccess) return GGA_ERR_CUDA;
   if (gga::launch_memory(h->view, reinterpret_cast<uint64_t*>(h->memstats), st) != GGA_OK) return GGA_ERR_CUDA;
   unsigned long long ms[2];
-  gga::PoolState ps;
-  if (cudaMemcpyAsync(ms, h->memstats, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaMemcpyAsync(&ps, h->view.pool, sizeof(ps), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return GGA_ERR_CUDA;
+  if (cudaMemcpyAsync(ms, h->memstats, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess) return GGA_ERR_CUDA;
+  uint64_t bump = 0, fb = 0;
+  const int rc = pool_read(h->pool, st, &bump, &fb);
+  if (rc != GGA_OK) return rc;
   out->bucket_bytes = ms[0];
   out->live_bytes = ms[1];
-  out->pool_bytes = h->p.pool_bytes;
-  out->pool_bump_bytes = ps.bump < ps.cap ? ps.bump : ps.cap;
-  uint64_t fb = 0;
-  for (int b = 0; b < gga::kMaxBuckets; ++b) {
-    const uint64_t bytes = gga::alloc_bytes_for(gga::bucket_len(b, h->log2B) * h->p.elem_bytes);
-    if (h->log2B + b < 64) fb += (ps.ring_tail[b] - ps.ring_head[b]) * bytes;
-  }
+  out->pool_bytes = h->pool->bytes;
+  out->pool_bump_bytes = bump;
   out->free_list_bytes = fb;
-  out->metadata_bytes = h->meta_bytes;
+  out->metadata_bytes = h->meta_bytes + (h->own_pool ? h->pool->ring_slots * 8 : 0);
   return GGA_OK;
 }
 
@@ -327,10 +438,12 @@ int gga_twophase_work(void* records_dev, uint64_t n, uint32_t passes, void* stre
 int gga_destroy(gga_handle h) {
   if (!h) return GGA_ERR_INVALID;
   int rc = GGA_OK;
+  // In a shared pool the buckets go back to its queues first.
+  if (!h->own_pool && h->pool && h->meta && gga::launch_clear(h->view, nullptr) != GGA_OK) rc = GGA_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) rc = GGA_ERR_CUDA;
   if (h->scratch && cudaFree(h->scratch) != cudaSuccess) rc = GGA_ERR_CUDA;
-  if (h->own_slab && h->slab && cudaFree(h->slab) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (h->meta && cudaFree(h->meta) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (h->own_pool && h->pool && pool_free(h->pool) != GGA_OK) rc = GGA_ERR_CUDA;
   delete h;
   return rc;
 }

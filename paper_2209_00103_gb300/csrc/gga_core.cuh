@@ -27,22 +27,25 @@ constexpr uint32_t kSpinLimit = 1u << 22;    // bound on spin waits (~0.5 s with
 constexpr uint32_t kChunkBytes = 16384;      // flatten / rw_b work unit
 
 // Device pool (Algorithm 2's malloc, without the host).  Buckets are carved
-// from one slab by a bump pointer; buckets handed back by gga_clear wait in
-// one ring queue per bucket index b (all of size B * 2^b * E) and are reused
-// first.  Queues are touched with atomicAdd only: insertion kernels pop
-// (ring_taken), gga_clear pushes (ring_tail), never both in one kernel, and
-// the single-threaded fix-up after each insertion folds the pops into
-// ring_head.  A handle's LFVectors hold at most one bucket of each index, so
-// a queue never holds more than L entries.
+// from one slab by a bump pointer; buckets handed back (gga_clear,
+// gga_destroy) wait in one ring queue per power-of-two byte class and are
+// reused first.  Queues are touched with atomicAdd only: insertion kernels
+// pop (ring_taken), clear kernels push (ring_tail), never both in one kernel,
+// and kernels using one pool are ordered on the device (one stream, or
+// events); a one-thread fix-up after each insertion folds the pops into
+// ring_head.  A class's queue has room for every bucket of that class the
+// slab can hold (or, for a handle's private pool, that its LFVectors can
+// hold), so pushes never overrun it.
 struct PoolState {
-  unsigned long long bump;                      // slab bytes handed out (passes cap once exhausted)
-  unsigned long long cap;                       // slab bytes
-  unsigned long long base;                      // slab address
-  unsigned long long ring_head[kMaxBuckets];    // first queued entry
-  unsigned long long ring_tail[kMaxBuckets];    // one past the last queued entry
-  unsigned long long ring_taken[kMaxBuckets];   // pops by the running insertion kernel
-  unsigned long long rings;                     // address of [kMaxBuckets][ring_cap] bucket addresses
-  unsigned long long ring_cap;
+  unsigned long long bump;                        // slab bytes handed out (passes cap once exhausted)
+  unsigned long long cap;                         // slab bytes
+  unsigned long long base;                        // slab address
+  unsigned long long ring_head[kPoolClasses];     // first queued entry
+  unsigned long long ring_tail[kPoolClasses];     // one past the last queued entry
+  unsigned long long ring_taken[kPoolClasses];    // pops by the running insertion kernel
+  unsigned long long ring_off[kPoolClasses];      // first slot of the class in `rings`
+  unsigned long long ring_cap[kPoolClasses];      // slots of the class (0: class not served)
+  unsigned long long rings;                       // address of the uint64 slots
 };
 
 struct ArrayView {
@@ -131,26 +134,40 @@ __host__ __device__ __forceinline__ uint64_t alloc_bytes_for(uint64_t bytes) {
   return bytes < kGrain ? kGrain : bytes;   // bucket sizes are powers of two
 }
 
-// Pop a queued bucket of index b, or 0 if the queue ran dry.
-__device__ __forceinline__ uint64_t ring_pop(PoolState* p, uint32_t b) {
-  const unsigned long long i = atomicAdd(&p->ring_taken[b], 1ull);
-  const unsigned long long pos = p->ring_head[b] + i;
-  if (pos >= p->ring_tail[b]) return 0;
-  return reinterpret_cast<const uint64_t*>(p->rings)[static_cast<uint64_t>(b) * p->ring_cap + pos % p->ring_cap];
+__host__ __device__ __forceinline__ uint32_t class_of(uint64_t bytes) {
+  const uint64_t a = alloc_bytes_for(bytes);
+  uint32_t c = 0;
+  while ((1ull << c) < a) ++c;
+  return c;
 }
 
-// Queue a bucket of index b (gga_clear only).
-__device__ __forceinline__ void ring_push(PoolState* p, uint32_t b, uint64_t addr) {
-  const unsigned long long j = atomicAdd(&p->ring_tail[b], 1ull);
-  reinterpret_cast<uint64_t*>(p->rings)[static_cast<uint64_t>(b) * p->ring_cap + j % p->ring_cap] = addr;
+// Pop a queued bucket of byte class c, or 0 if the queue ran dry.
+__device__ __forceinline__ uint64_t ring_pop(PoolState* p, uint32_t c) {
+  const unsigned long long rc = p->ring_cap[c];
+  if (rc == 0) return 0;
+  const unsigned long long i = atomicAdd(&p->ring_taken[c], 1ull);
+  const unsigned long long pos = p->ring_head[c] + i;
+  if (pos >= p->ring_tail[c]) return 0;
+  return reinterpret_cast<const uint64_t*>(p->rings)[p->ring_off[c] + pos % rc];
+}
+
+// Queue a bucket of byte class c (clear kernels only).  Returns false if the
+// pool does not serve the class.
+__device__ __forceinline__ bool ring_push(PoolState* p, uint32_t c, uint64_t addr) {
+  const unsigned long long rc = p->ring_cap[c];
+  if (rc == 0) return false;
+  const unsigned long long j = atomicAdd(&p->ring_tail[c], 1ull);
+  reinterpret_cast<uint64_t*>(p->rings)[p->ring_off[c] + j % rc] = addr;
+  return true;
 }
 
 // After an insertion kernel: fold its pops into the queue heads (one thread).
 __device__ __forceinline__ void ring_fixup(PoolState* p) {
-  for (int b = 0; b < kMaxBuckets; ++b) {
-    const unsigned long long h = p->ring_head[b] + p->ring_taken[b];
-    p->ring_head[b] = h < p->ring_tail[b] ? h : p->ring_tail[b];
-    p->ring_taken[b] = 0;
+  for (int c = 0; c < kPoolClasses; ++c) {
+    if (p->ring_cap[c] == 0) continue;
+    const unsigned long long h = p->ring_head[c] + p->ring_taken[c];
+    p->ring_head[c] = h < p->ring_tail[c] ? h : p->ring_tail[c];
+    p->ring_taken[c] = 0;
   }
 }
 
@@ -165,7 +182,7 @@ __device__ inline uint32_t grow_buckets(const ArrayView& v, uint32_t l, uint32_t
   uint64_t miss = 0, bump_bytes = 0;
   for (uint32_t b = nb; b < need; ++b) {
     if (tab[b] != 0) continue;
-    const uint64_t a = ring_pop(v.pool, b);
+    const uint64_t a = ring_pop(v.pool, class_of(bucket_len(b, v.log2B) * v.E));
     if (a) {
       tab[b] = a;
     } else {

@@ -35,7 +35,9 @@ MAX_THRESHOLDS = 16
 # Every symbol include/gga.h declares.
 EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
-            "gga_destroy", "gga_twophase_spawn", "gga_twophase_work"]
+            "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
+            "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
+            "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy"]
 
 
 class gga_params(ctypes.Structure):
@@ -49,6 +51,10 @@ class gga_gen_spec(ctypes.Structure):
                 ("thresholds", ctypes.c_uint32 * MAX_THRESHOLDS), ("va", ctypes.c_uint64),
                 ("vb", ctypes.c_uint64), ("vc", ctypes.c_uint64), ("round0", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32)]
+
+
+class gga_batch_job(ctypes.Structure):
+    _fields_ = [("array", ctypes.c_void_p), ("spec", gga_gen_spec), ("target", ctypes.c_uint64)]
 
 
 class gga_mem(ctypes.Structure):
@@ -88,6 +94,16 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_last_error": [vp, vp],
         "gga_destroy": [vp],
         "gga_twophase_spawn": [vp, u32, u64, i32, vp, vp],
+        "gga_pool_create": [u64, vp, u64, vp, ctypes.POINTER(vp)],
+        "gga_pool_destroy": [vp],
+        "gga_pool_info": [vp, ctypes.POINTER(u64), vp],
+        "gga_create_in_pool": [ctypes.POINTER(gga_params), vp, vp, ctypes.POINTER(vp)],
+        "gga_batch_create": [ctypes.POINTER(gga_batch_job), u32, vp, ctypes.POINTER(vp)],
+        "gga_batch_grow": [vp, vp],
+        "gga_batch_clear": [vp, vp],
+        "gga_batch_capture": [vp, vp],
+        "gga_batch_replay": [vp, vp],
+        "gga_batch_destroy": [vp],
         "gga_twophase_work": [vp, u64, u32, vp],
     }
     for name, args in sig.items():
@@ -145,6 +161,33 @@ def gga_create(L: int, T: int, B: int, E: int, pool_bytes: int, pool: torch.Tens
     h = ctypes.c_void_p()
     _check(lib.gga_create(ctypes.byref(p), _dptr(pool) if pool is not None else None, _stream(stream),
                           ctypes.byref(h)), "gga_create")
+    return h
+
+
+def gga_pool_create(pool_bytes: int, min_bucket_bytes: int, slab: torch.Tensor | None = None,
+                    stream=None) -> ctypes.c_void_p:
+    pl = ctypes.c_void_p()
+    _check(load_library().gga_pool_create(pool_bytes, _dptr(slab) if slab is not None else None, min_bucket_bytes,
+                                          _stream(stream), ctypes.byref(pl)), "gga_pool_create")
+    return pl
+
+
+def gga_pool_destroy(pool):
+    _check(load_library().gga_pool_destroy(pool), "gga_pool_destroy")
+
+
+def gga_pool_info(pool, stream=None) -> dict:
+    out = (ctypes.c_uint64 * 4)()
+    _check(load_library().gga_pool_info(pool, out, _stream(stream)), "gga_pool_info")
+    return {"pool_bytes": int(out[0]), "bump_bytes": int(out[1]), "free_list_bytes": int(out[2]),
+            "queue_bytes": int(out[3])}
+
+
+def gga_create_in_pool(L: int, T: int, B: int, E: int, pool, stream=None) -> ctypes.c_void_p:
+    p = gga_params(L, T, B, E, 0, 0)
+    h = ctypes.c_void_p()
+    _check(load_library().gga_create_in_pool(ctypes.byref(p), pool, _stream(stream), ctypes.byref(h)),
+           "gga_create_in_pool")
     return h
 
 
@@ -251,19 +294,86 @@ def gga_twophase_work(records: torch.Tensor, passes: int, stream=None):
            "gga_twophase_work")
 
 
+class GGABatch:
+    """Many GGArrays grown to their targets in one persistent launch (see
+    gga_batch_create).  jobs: list of (GGArray, gga_gen_spec, target)."""
+
+    def __init__(self, jobs, stream=None):
+        self._arrays = [j[0] for j in jobs]
+        arr = (gga_batch_job * max(1, len(jobs)))()
+        for i, (g, spec, target) in enumerate(jobs):
+            arr[i].array = g.h
+            arr[i].spec = spec
+            arr[i].target = int(target)
+        self.h = ctypes.c_void_p()
+        _check(load_library().gga_batch_create(arr, len(jobs), _stream(stream), ctypes.byref(self.h)),
+               "gga_batch_create")
+
+    def grow(self, stream=None):
+        _check(load_library().gga_batch_grow(self.h, _stream(stream)), "gga_batch_grow")
+
+    def clear(self, stream=None):
+        _check(load_library().gga_batch_clear(self.h, _stream(stream)), "gga_batch_clear")
+
+    def capture(self, stream):
+        _check(load_library().gga_batch_capture(self.h, _stream(stream)), "gga_batch_capture")
+
+    def replay(self, stream=None):
+        _check(load_library().gga_batch_replay(self.h, _stream(stream)), "gga_batch_replay")
+
+    def close(self):
+        if self.h:
+            _check(load_library().gga_batch_destroy(self.h), "gga_batch_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---------------------------------------------------------------------------
 # Object wrapper.
 
+class GGAPool:
+    """A bucket pool shared by several GGArrays (see gga_pool_create)."""
+
+    def __init__(self, pool_bytes: int, min_bucket_bytes: int, slab: torch.Tensor | None = None, stream=None):
+        self._slab = slab
+        self.h = gga_pool_create(pool_bytes, min_bucket_bytes, slab, stream)
+
+    def info(self, stream=None) -> dict:
+        return gga_pool_info(self.h, stream)
+
+    def close(self):
+        if self.h:
+            gga_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class GGArray:
     """A GGArray on the current CUDA device (L LFVectors of T-thread blocks,
-    first bucket B elements, E-byte elements, bucket pool of pool_bytes)."""
+    first bucket B elements, E-byte elements).  Buckets come from a private
+    pool of pool_bytes (optionally on a lent slab tensor), or from a shared
+    GGAPool."""
 
-    def __init__(self, L: int, T: int, B: int, E: int, pool_bytes: int, pool: torch.Tensor | None = None,
-                 stream=None):
+    def __init__(self, L: int, T: int, B: int, E: int, pool_bytes: int = 0, pool: torch.Tensor | None = None,
+                 stream=None, shared_pool: GGAPool | None = None):
         self.L, self.T, self.B, self.E = L, T, B, E
         self.pool_bytes = pool_bytes
         self._pool = pool
-        self.h = gga_create(L, T, B, E, pool_bytes, pool, stream)
+        self._shared = shared_pool
+        if shared_pool is not None:
+            self.h = gga_create_in_pool(L, T, B, E, shared_pool.h, stream)
+        else:
+            self.h = gga_create(L, T, B, E, pool_bytes, pool, stream)
 
     def insert(self, counts, values, stream=None):
         gga_insert(self.h, counts, values, stream)

@@ -391,3 +391,25 @@ def test_split_counts_and_initial_records():
     r = wl.initial_records(2048)
     assert r["pos"][1024] == 0 and r["pos"][1023] == 1023
     assert r["vel"][1] == 7 / 16 and r["vel"][3] == 5 / 16
+
+
+# --------------------------------------------------------------------------
+# Growth to a target (batched arrays): sizes are the targets split over the
+# LFVectors, and each LFVector is the prefix of the unclipped sequence the
+# same draws produce (clipping by the scan = truncation in insertion order).
+
+@pytest.mark.parametrize("dist", ["bernoulli", "uniform3", "geometric", "poisson"])
+@pytest.mark.parametrize("E", [4, 8, 16])
+def test_grow_to_target_is_a_truncated_generation(dist, E):
+    L, T, B = 5, 24, 4
+    thr = wl.poisson1_thresholds()
+    coeffs = (0x10001, 0x9E3779B9, 7)
+    for target in [0, 1, 4, 37, 1000, 4099]:
+        a = oracle.OracleGGArray(L, T, B, E)
+        a.grow_to_target(11, dist, coeffs, target, round0=3, thresholds=thr)
+        per = [target // L + (1 if l < target % L else 0) for l in range(L)]
+        assert a.sizes().tolist() == per
+        full = oracle.OracleGGArray(L, T, B, E)
+        full.insert_generated(11, dist, coeffs, 3, 600, thresholds=thr)
+        for l in range(L):
+            assert a.lfvector(l).tobytes() == full.lfvector(l)[:per[l]].tobytes()
