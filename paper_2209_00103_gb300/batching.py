@@ -150,3 +150,39 @@ def tuned_rule() -> Rule:
             return Rule(**json.load(f)["chosen"])
     except (OSError, KeyError, ValueError, TypeError):
         return Rule()
+
+
+def plain_time(arrays, sizes, stream, steps: int = 3) -> float:
+    """Milliseconds to grow every array with its own launches, one array
+    after another (the plain one-launch-per-array form), median of steps."""
+    import torch
+    from . import gga
+    singles = [gga.GGABatch([(g, spec_for(gga, a), int(s))], stream=stream)
+               for a, (g, s) in enumerate(zip(arrays, sizes))]
+    times = []
+    for _ in range(steps + 1):
+        for b in singles:
+            b.clear(stream)
+        a_ev = torch.cuda.Event(enable_timing=True)
+        b_ev = torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        for b in singles:
+            b.grow(stream)
+        b_ev.record(stream)
+        torch.cuda.synchronize()
+        times.append(a_ev.elapsed_time(b_ev))
+    for b in singles:
+        b.close()
+    return sorted(times[1:])[len(times[1:]) // 2]
+
+
+if __name__ == "__main__":
+    import argparse
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--autotune", metavar="OUT_JSON", help="measure the candidate rules, write the choice here")
+    args = ap.parse_args()
+    if args.autotune:
+        s = torch.cuda.Stream()
+        rule = autotune(batched_sizes(), s, out_path=args.autotune)
+        print("chosen", rule)
