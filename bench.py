@@ -52,8 +52,10 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--workload", choices=["paper_growth", "batched"], default="paper_growth",
-                    help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch")
+    ap.add_argument("--workload", choices=["paper_growth", "batched", "served"], default="paper_growth",
+                    help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch; "
+                         "served: continuous-batching request server")
+    ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of offered load")
     return ap.parse_args()
 
 
@@ -550,6 +552,35 @@ def run_batched(args, world, rank, local):
     return res
 
 
+def run_served(args, world, rank, local):
+    """Poisson arrivals (20k req/s) over 65,536 live int64 arrays in a 64 GiB
+    pool: 70% appends (n log-uniform 1..1M), 25% reads of 4096 random
+    indices, 5% flattens that retire the array.  The same trace runs through
+    the continuous-batching server and through the plain serial form (one
+    request per launch sequence, each waited for)."""
+    from paper_2209_00103_gb300 import serving
+    cfg = serving.ServeConfig(duration=args.duration)
+    trace = serving.make_trace(cfg)
+    srv = serving.Server(cfg)
+    sampler = ClockSampler(local)
+    sampler.start()
+    rep = srv.run(trace, batched=True)
+    clocks = sampler.stop()
+    srv.close()
+    plain = serving.Server(cfg)
+    rep_plain = plain.run(trace, batched=False)
+    plain.close()
+    return {"metric": "served GGArray p99 latency (ms), continuous batching", "value": rep["p99_ms"], "unit": "ms",
+            "n_gpus": world, "steps": rep["completed"], "warmup": 0,
+            "ms_per_step": round(rep["wall_s"] * 1e3 / max(1, rep["completed"]), 5), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "served_65536_int64_arrays_poisson20k_70_25_5_pool64GiB",
+                       "duration_s": cfg.duration, "requests": int(len(trace[0])), "arrays": cfg.n_arrays,
+                       "L": cfg.L, "T": cfg.T, "B": cfg.B, "pool_bytes": cfg.pool_bytes,
+                       "deadline_s": cfg.deadline, "max_inflight_steps": cfg.max_inflight},
+            "served": rep, "plain_one_launch_per_request": rep_plain, "clocks": clocks}
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -557,6 +588,8 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload == "batched":
         res = run_batched(args, world, rank, local)
+    elif args.workload == "served":
+        res = run_served(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -335,6 +335,45 @@ int gga_batch_replay(gga_batch b, void* stream);
 /* gga_batch_destroy -- free the batch's tables (not its arrays). */
 int gga_batch_destroy(gga_batch b);
 
+/*
+ * Request batches for serving many live arrays (continuous batching: the
+ * requests that arrived while earlier work ran are launched together).
+ *
+ * gga_append_batch -- append reqs[i].n elements to reqs[i].array for all i,
+ * in one launch (one block per (request, LFVector): one reservation, the
+ * buckets it reaches from the pool, then the writes).  Every LFVector l of
+ * the array gets n / L elements, one more for the first n % L; element k
+ * appended to LFVector l has the value tag * 2^24 + l * 2^20 + k (stored as
+ * E bytes like gga_insert_generated's values), so n / L must be below 2^20.
+ * All arrays must share one pool and appear at most once (GGA_ERR_INVALID).
+ * If the pool cannot hold an LFVector's share, that LFVector takes none of
+ * it and GGA_ERR_POOL_EXHAUSTED is latched (callers admit requests so that
+ * this does not happen).
+ */
+typedef struct {
+  gga_handle array;
+  uint64_t n;
+  uint64_t tag;
+} gga_append_req;
+
+int gga_append_batch(const gga_append_req* reqs, uint32_t n, void* stream);
+
+/*
+ * gga_read_batch -- for every request, read n elements at global indices
+ * floor(u_k * N / 2^32), u_k = the high 32 bits of SplitMix64 output k + 1
+ * of the stream seeded with `seed`, N = the array's size when the read runs
+ * (Sec. IV's global indexing), into out (device, n elements of E bytes;
+ * zeros if the array is empty).  One block per request.
+ */
+typedef struct {
+  gga_handle array;
+  uint64_t n;
+  uint64_t seed;
+  void* out;
+} gga_read_req;
+
+int gga_read_batch(const gga_read_req* reqs, uint32_t n, void* stream);
+
 /* gga_destroy -- free the handle's metadata and its private pool (a borrowed
  * slab is left to its owner); an array of a shared pool first returns its
  * buckets to the pool.  Synchronizes the device. */

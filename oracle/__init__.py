@@ -89,6 +89,10 @@ def _load():
         lib.orc_grow_to_target.argtypes = [
             ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, u8p, ctypes.c_uint32, ctypes.c_uint64,
             ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32]
+        lib.orc_append.restype = ctypes.c_int
+        lib.orc_append.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_read_random.restype = ctypes.c_int
+        lib.orc_read_random.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, u8p]
         lib.orc_spawn.restype = ctypes.c_int
         lib.orc_spawn.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, u8p]
         lib.orc_work_passes.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint32]
@@ -171,6 +175,15 @@ class OracleGGArray:
         rc = self._lib.orc_grow_to_target(self._h, seed & 0xFFFFFFFFFFFFFFFF, DIST[dist], _ptr(thr),
                                           0 if thr is None else len(thr), va, vb, vc, round0, target, max_rounds)
         self._check(rc, "grow_to_target")
+
+    def append(self, n: int, tag: int):
+        """Served append (see orc_append)."""
+        self._check(self._lib.orc_append(self._h, n, tag & 0xFFFFFFFFFFFFFFFF), "append")
+
+    def read_random(self, n: int, seed: int) -> np.ndarray:
+        out = np.zeros(max(n, 1), dtype=self.dtype)
+        self._check(self._lib.orc_read_random(self._h, n, seed & 0xFFFFFFFFFFFFFFFF, _ptr(out)), "read_random")
+        return out[:n]
 
     def size(self) -> int:
         return int(self._lib.orc_size(self._h))

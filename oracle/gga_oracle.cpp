@@ -296,6 +296,43 @@ int orc_grow_to_target(void* h, uint64_t seed, uint32_t dist, const uint32_t* th
   return ORC_OK;
 }
 
+// Served append: LFVector l receives n / L elements (one more for the first
+// n % L), element k with value tag * 2^24 + l * 2^20 + k, appended in order.
+int orc_append(void* h, uint64_t n, uint64_t tag) {
+  OracleArray& a = *static_cast<OracleArray*>(h);
+  std::vector<unsigned char> e(a.E);
+  for (uint32_t l = 0; l < a.L; ++l) {
+    const uint64_t c = n / a.L + (l < n % a.L ? 1 : 0);
+    for (uint64_t k = 0; k < c; ++k) {
+      make_value(tag * (1ULL << 24) + static_cast<uint64_t>(l) * (1ULL << 20) + k, a.E, e.data());
+      a.lfv[l].insert(a.lfv[l].end(), e.begin(), e.end());
+    }
+  }
+  return ORC_OK;
+}
+
+// Served random read: out[k] = element at global index
+// floor((splitmix_at(seed, k) >> 32) * N / 2^32), N = current size; zeros if
+// the array is empty (Sec. IV's global indexing through the prefix sum).
+int orc_read_random(void* h, uint64_t n, uint64_t seed, void* out) {
+  OracleArray& a = *static_cast<OracleArray*>(h);
+  std::vector<uint64_t> off = prefix_offsets(a);
+  const uint64_t N = off.back();
+  unsigned char* dst = static_cast<unsigned char*>(out);
+  for (uint64_t k = 0; k < n; ++k) {
+    if (N == 0) {
+      std::memset(dst + k * a.E, 0, a.E);
+      continue;
+    }
+    const uint64_t g = ((splitmix_at(seed, k) >> 32) * N) >> 32;
+    uint32_t l;
+    uint64_t j;
+    locate(off, g, &l, &j);
+    std::memcpy(dst + k * a.E, a.lfv[l].data() + j * a.E, a.E);
+  }
+  return ORC_OK;
+}
+
 // Global size (Sec. IV: the GGArray keeps the global size).
 uint64_t orc_size(void* h) {
   OracleArray& a = *static_cast<OracleArray*>(h);

@@ -43,6 +43,7 @@ struct gga_array {
   gga::ArrayView view;
   gga::InsertScratch ins;   // pointers into meta (fixed part) and scratch (per-call part)
   unsigned long long* memstats;
+  gga::ArrayView* dview;    // device copy of `view`, for kernels that take many arrays
 };
 
 namespace {
@@ -199,6 +200,9 @@ int sync_status(gga_array* h, cudaStream_t st, bool clear) {
 }  // namespace
 
 namespace gga {
+ArrayView* handle_dview(gga_handle h) { return h ? h->dview : nullptr; }
+PoolState* handle_pool(gga_handle h) { return h ? h->pool->state : nullptr; }
+
 bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device, int* num_sms) {
   if (!h) return false;
   *view = h->view;
@@ -232,7 +236,8 @@ static int handle_make(const gga_params* p, gga_pool_t* pool, bool own_pool, cud
   };
   const size_t o_sizes = take(L * 8), o_offsets = take((L + 1) * 8), o_buckets = take(L * gga::kMaxBuckets * 8),
                o_nb = take(L * 4), o_fl = take((L + 1) * 8), o_ib = take(L * 8), o_il = take(L * 8),
-               o_cp = take((L + 1) * 8), o_status = take(4), o_counters = take(16), o_mem = take(16);
+               o_cp = take((L + 1) * 8), o_status = take(4), o_counters = take(16), o_mem = take(16),
+               o_view = take(sizeof(gga::ArrayView));
   h->meta_bytes = off;
   if (cudaMalloc(&h->meta, h->meta_bytes) != cudaSuccess) {
     delete h;
@@ -260,8 +265,12 @@ static int handle_make(const gga_params* p, gga_pool_t* pool, bool own_pool, cud
   h->scratch = nullptr;
   h->scratch_bytes = 0;
   h->scratch_rounds = 0;
+  h->dview = reinterpret_cast<gga::ArrayView*>(m + o_view);
   int rc = cudaMemsetAsync(h->meta, 0, h->meta_bytes, st) == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
-  if (rc == GGA_OK) rc = ensure_scratch(h, 64, st);
+  if (rc == GGA_OK && cudaMemcpyAsync(h->dview, &h->view, sizeof(gga::ArrayView), cudaMemcpyHostToDevice, st) !=
+                          cudaSuccess)
+    rc = GGA_ERR_CUDA;
+  // The insertion scratch is made by the first gga_insert that needs it.
   if (rc == GGA_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (rc != GGA_OK) {
     h->own_pool = false;   // the caller disposes of the pool

@@ -37,7 +37,7 @@ EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_insert_genera
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
-            "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy"]
+            "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy", "gga_append_batch", "gga_read_batch"]
 
 
 class gga_params(ctypes.Structure):
@@ -55,6 +55,15 @@ class gga_gen_spec(ctypes.Structure):
 
 class gga_batch_job(ctypes.Structure):
     _fields_ = [("array", ctypes.c_void_p), ("spec", gga_gen_spec), ("target", ctypes.c_uint64)]
+
+
+class gga_append_req(ctypes.Structure):
+    _fields_ = [("array", ctypes.c_void_p), ("n", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class gga_read_req(ctypes.Structure):
+    _fields_ = [("array", ctypes.c_void_p), ("n", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("out", ctypes.c_void_p)]
 
 
 class gga_mem(ctypes.Structure):
@@ -104,6 +113,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_batch_capture": [vp, vp],
         "gga_batch_replay": [vp, vp],
         "gga_batch_destroy": [vp],
+        "gga_append_batch": [ctypes.POINTER(gga_append_req), u32, vp],
+        "gga_read_batch": [ctypes.POINTER(gga_read_req), u32, vp],
         "gga_twophase_work": [vp, u64, u32, vp],
     }
     for name, args in sig.items():
@@ -292,6 +303,23 @@ def gga_twophase_work(records: torch.Tensor, passes: int, stream=None):
     """pos += vel, `passes` streaming passes over flattened records ([n, 2] int64)."""
     _check(load_library().gga_twophase_work(_dptr(records), records.shape[0], passes, _stream(stream)),
            "gga_twophase_work")
+
+
+def gga_append_batch(reqs, stream=None):
+    """reqs: list of (GGArray, n, tag)."""
+    arr = (gga_append_req * max(1, len(reqs)))()
+    for i, (g, n, tag) in enumerate(reqs):
+        arr[i].array, arr[i].n, arr[i].tag = g.h, int(n), int(tag) & 0xFFFFFFFFFFFFFFFF
+    _check(load_library().gga_append_batch(arr, len(reqs), _stream(stream)), "gga_append_batch")
+
+
+def gga_read_batch(reqs, stream=None):
+    """reqs: list of (GGArray, n, seed, out tensor)."""
+    arr = (gga_read_req * max(1, len(reqs)))()
+    for i, (g, n, seed, out) in enumerate(reqs):
+        arr[i].array, arr[i].n, arr[i].seed = g.h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF
+        arr[i].out = out.data_ptr()
+    _check(load_library().gga_read_batch(arr, len(reqs), _stream(stream)), "gga_read_batch")
 
 
 class GGABatch:

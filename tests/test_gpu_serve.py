@@ -1,0 +1,107 @@
+"""Serving many live arrays: batched appends and random reads against the
+oracle, and the continuous-batching server: every request's result is the
+same when it runs in a mix (batched) and alone (one request per launch),
+and both equal the oracle's replay of the requests in arrival order."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2209_00103_gb300 import gga, serving
+
+from harness import assert_same_state, dev_to_np
+
+pytestmark = pytest.mark.gpu
+
+
+def test_append_and_read_batches_match_oracle():
+    rng = np.random.default_rng(83)
+    pool = gga.GGAPool(512 << 20, 1024 * 4)
+    shapes = [(int(rng.choice([1, 2, 4, 7])), 256, 1024, int(rng.choice([4, 8, 16]))) for _ in range(20)]
+    arrays = [gga.GGArray(L, T, B, E, shared_pool=pool) for (L, T, B, E) in shapes]
+    refs = [oracle.OracleGGArray(L, T, B, E) for (L, T, B, E) in shapes]
+    tag = 1
+    for step in range(6):
+        picks = rng.choice(len(arrays), size=8, replace=False)
+        reqs = []
+        for a in picks:
+            n = int(rng.choice([0, 1, 5, 1000, 70000]))
+            reqs.append((arrays[a], n, tag))
+            refs[a].append(n, tag)
+            tag += 1
+        gga.gga_append_batch(reqs)
+        reads = []
+        for a in rng.choice(len(arrays), size=6, replace=False):
+            out = gga.elem_tensor(4096, shapes[a][3])
+            reads.append((arrays[a], 4096, 1000 + step * 10 + int(a), out, a))
+        gga.gga_read_batch([(g, n, seed, out) for g, n, seed, out, _ in reads])
+        for g, n, seed, out, a in reads:
+            assert dev_to_np(out, shapes[a][3]).tobytes() == refs[a].read_random(n, seed).tobytes()
+    for g, o in zip(arrays, refs):
+        assert_same_state(g, o)
+    with pytest.raises(gga.GGAError):                     # one request per array per launch
+        gga.gga_append_batch([(arrays[0], 1, 1), (arrays[0], 1, 2)])
+    for g in arrays:
+        g.close()
+    pool.close()
+
+
+def small_cfg(**kw):
+    base = dict(n_arrays=64, L=4, T=256, B=1024, E=8, pool_bytes=2 << 30, rate=20000.0, duration=0.25,
+                max_append=50000, deadline=1.0, max_inflight=3, max_batch=480, flatten_arena_bytes=1 << 30)
+    base.update(kw)
+    return serving.ServeConfig(**base)
+
+
+def replay_oracle(cfg, trace, state):
+    t, typ, arr, nn, tag = trace
+    refs = [oracle.OracleGGArray(cfg.L, cfg.T, cfg.B, cfg.E) for _ in range(cfg.n_arrays)]
+    out = {}
+    for r in range(len(t)):
+        if state is not None and state[r] != 1:
+            continue
+        o = refs[arr[r]]
+        if typ[r] == serving.APPEND:
+            o.append(int(nn[r]), int(tag[r]))
+        elif typ[r] == serving.READ:
+            out[r] = o.read_random(cfg.read_n, int(tag[r]))
+        else:
+            out[r] = o.flatten().copy()
+            refs[arr[r]] = oracle.OracleGGArray(cfg.L, cfg.T, cfg.B, cfg.E)   # retired
+    return out
+
+
+def test_server_mix_equals_alone_equals_oracle():
+    cfg = small_cfg()
+    trace = serving.make_trace(cfg)
+    mixed = serving.Server(cfg, record=True)
+    rep_mix = mixed.run(trace, batched=True)
+    res_mix = mixed.results
+    mixed.close()
+    alone = serving.Server(cfg, record=True)
+    rep_alone = alone.run(trace, batched=False)
+    res_alone = alone.results
+    alone.close()
+    assert rep_mix["rejected"] == 0 and rep_alone["rejected"] == 0
+    assert rep_mix["completed"] == len(trace[0]) == rep_alone["completed"]
+    want = replay_oracle(cfg, trace, None)
+    assert set(res_mix) == set(res_alone) == set(want)
+    for r in want:
+        assert res_mix[r].tobytes() == want[r].view(np.int64).tobytes(), r
+        assert res_alone[r].tobytes() == res_mix[r].tobytes(), r
+
+
+def test_server_admission_under_a_full_pool():
+    # A pool far too small for the offered appends: appends wait, then some
+    # are rejected at the deadline; admitted ones never fail on the device.
+    cfg = small_cfg(pool_bytes=48 << 20, duration=0.2, deadline=0.02, max_append=200000)
+    trace = serving.make_trace(cfg)
+    srv = serving.Server(cfg)
+    rep = srv.run(trace, batched=True)
+    assert rep["rejected"] > 0
+    assert rep["completed"] + rep["rejected"] == len(trace[0])
+    assert all(st.g.last_error() == gga.GGA_OK for st in srv.arrays)
+    info = srv.pool.info()
+    assert info["bump_bytes"] <= cfg.pool_bytes
+    srv.close()

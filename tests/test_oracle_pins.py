@@ -413,3 +413,37 @@ def test_grow_to_target_is_a_truncated_generation(dist, E):
         full.insert_generated(11, dist, coeffs, 3, 600, thresholds=thr)
         for l in range(L):
             assert a.lfvector(l).tobytes() == full.lfvector(l)[:per[l]].tobytes()
+
+
+# --------------------------------------------------------------------------
+# Served appends and random reads.
+
+def test_served_append_values_decode():
+    L, T, B = 4, 8, 16
+    a = oracle.OracleGGArray(L, T, B, 8)
+    plan = [(10, 7), (1, 8), (0, 9), (1003, 10)]
+    for n, tag in plan:
+        a.append(n, tag)
+    want_sizes = np.zeros(L, dtype=np.uint64)
+    for n, _ in plan:
+        want_sizes += np.array([n // L + (1 if l < n % L else 0) for l in range(L)], dtype=np.uint64)
+    assert np.array_equal(a.sizes(), want_sizes)
+    for l in range(L):
+        v = a.lfvector(l).astype(np.uint64)
+        tag, ll, k = v >> np.uint64(24), (v >> np.uint64(20)) & np.uint64(15), v & np.uint64((1 << 20) - 1)
+        assert np.all(ll == l)
+        # appended in request order, each request's share in k order
+        exp = np.concatenate([np.stack([np.full(c, t, dtype=np.uint64), np.arange(c, dtype=np.uint64)], 1)
+                              for n, t in plan for c in [n // L + (1 if l < n % L else 0)]])
+        assert np.array_equal(np.stack([tag, k], 1), exp)
+
+
+def test_served_random_read_matches_uniform_indices():
+    L, T, B = 3, 8, 16
+    a = oracle.OracleGGArray(L, T, B, 8)
+    assert not a.read_random(5, 1).any()                      # empty array reads zeros
+    a.append(10007, 3)
+    flat = a.flatten()
+    got = a.read_random(4096, 99)
+    idx = wl.uniform_indices(99, 4096, a.size())
+    assert np.array_equal(got, flat[idx.astype(np.int64)])
