@@ -52,10 +52,14 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--workload", choices=["paper_growth", "batched", "served"], default="paper_growth",
+    ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase"],
+                    default="paper_growth",
                     help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch; "
                          "served: continuous-batching request server")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of offered load")
+    ap.add_argument("--newborn", action="store_true", help="two_phase: only the previous generation spawns")
+    ap.add_argument("--deadline", type=float, default=None,
+                    help="served: seconds an append may wait for pool memory before it is rejected")
     return ap.parse_args()
 
 
@@ -67,8 +71,8 @@ KERNEL_SOURCES = {
     "flatten_kernel": ["gga_access.cu", "gga_core.cuh"],
     "sweep_b_kernel": ["gga_access.cu", "gga_core.cuh"],
     "sweep_g_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "copy_bulk_kernel": ["gga_insert.cu", "gga_core.cuh"],
-    "count_kernel": ["gga_insert.cu", "gga_core.cuh"],
+    "copy_bulk_kernel": ["gga_insert.cu", "gga_core.cuh", "gga_gen.cuh"],
+    "count_kernel": ["gga_insert.cu", "gga_core.cuh", "gga_gen.cuh"],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_paper_growth_1024x512_B4096_R512.md")
 
@@ -560,6 +564,8 @@ def run_served(args, world, rank, local):
     request per launch sequence, each waited for)."""
     from paper_2209_00103_gb300 import serving
     cfg = serving.ServeConfig(duration=args.duration)
+    if args.deadline is not None:
+        cfg.deadline = args.deadline
     trace = serving.make_trace(cfg)
     srv = serving.Server(cfg)
     sampler = ClockSampler(local)
@@ -581,6 +587,70 @@ def run_served(args, world, rank, local):
             "served": rep, "plain_one_launch_per_request": rep_plain, "clocks": clocks}
 
 
+def run_two_phase(args, world, rank, local):
+    """The case study of the paper's Sec. VI-D: 2^24 initial 16-byte records
+    over 1024 LFVectors x 512 threads, 8 generations of Geometric(1/2)-1
+    children per record pushed back from inside the application kernel,
+    then flatten and 20 streaming passes of pos += vel on the contiguous copy."""
+    import numpy as np
+    from paper_2209_00103_gb300 import gga
+    from paper_2209_00103_gb300 import workloads as wl
+    w = wl.two_phase(only_newborn=args.newborn)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    counts = torch.from_numpy(wl.split_counts(w.L, w.T, w.n0).view(np.int32)).to(dev)
+    recs = wl.initial_records_t(w.n0, dev)
+    free, _ = torch.cuda.mem_get_info(dev)
+    final_est = w.n0 * (w.generations + 1 if w.only_newborn else 2 ** w.generations)
+    pool_bytes = int(min(2.3 * final_est * 16 + (1 << 30), free - final_est * 16 * 1.05 - (4 << 30)))
+    g = gga.GGArray(w.L, w.T, w.B, 16, pool_bytes)
+    born = torch.zeros(w.L, dtype=torch.int64, device=dev) if w.only_newborn else None
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(w.generations + 4)]
+    ev[0].record(stream)
+    g.insert(counts, recs, stream)
+    ev[1].record(stream)
+    for gen in range(w.generations):
+        gga.gga_twophase_spawn(g.h, gen, w.seed, born, stream)
+        ev[2 + gen].record(stream)
+    n, rc = g.size(stream)
+    if rc != gga.GGA_OK:
+        raise RuntimeError(f"device error {rc}")
+    mem = g.memory(stream)
+    dst = gga.elem_tensor(n, 16, dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    c = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    g.flatten(dst, stream)
+    b.record(stream)
+    gga.gga_twophase_work(dst, w.passes, stream)
+    c.record(stream)
+    torch.cuda.synchronize(dev)
+    spawn_ms = ev[1].elapsed_time(ev[1 + w.generations])
+    flat_ms = a.elapsed_time(b)
+    work_ms = b.elapsed_time(c)
+    peak, _ = peaks()
+    spawned = n - w.n0
+    res = {"metric": "two-phase case study: spawned records/s; flatten and work-pass GB/s",
+           "value": round(spawned / (spawn_ms / 1e3) / 1e9, 3), "unit": "Grecords/s", "n_gpus": world,
+           "steps": 1, "warmup": 0, "ms_per_step": round(ev[0].elapsed_time(ev[1 + w.generations]) + flat_ms + work_ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64/f32 records",
+           "data": "synthetic",
+           "config": {"workload": w.name, "initial_records": w.n0, "generations": w.generations,
+                      "final_records": n, "spawning": "newborn" if w.only_newborn else "all records",
+                      "passes": w.passes},
+           "phases_ms": {"initial_insert": round(ev[0].elapsed_time(ev[1]), 3),
+                         "spawn_generations": [round(ev[1 + k].elapsed_time(ev[2 + k]), 3) for k in range(w.generations)],
+                         "flatten": round(flat_ms, 3), "work_passes": round(work_ms, 3)},
+           "flatten_gbs": round(2 * n * 16 / (flat_ms / 1e3) / 1e9, 1),
+           "flatten_frac_of_measured_peak": round(2 * n * 16 / (flat_ms / 1e3) / 1e9 / peak, 3),
+           "work_pass_gbs_aos": round(w.passes * 32 * n / (work_ms / 1e3) / 1e9, 1),
+           "spawn_gbs": round((spawned * 16 + (n - spawned) * 16) / (spawn_ms / 1e3) / 1e9, 1),
+           "mem_over_needed": round(mem["bucket_bytes"] / max(1, mem["live_bytes"]), 4)}
+    g.close()
+    return res
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -590,6 +660,8 @@ def main():
         res = run_batched(args, world, rank, local)
     elif args.workload == "served":
         res = run_served(args, world, rank, local)
+    elif args.workload == "two_phase":
+        res = run_two_phase(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -8,6 +8,7 @@
 // lays out memory and enqueues launches.
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "gga_core.cuh"
@@ -26,6 +27,9 @@ struct gga_pool_t {
   uint64_t bytes;
   uint64_t min_bucket_bytes;
   int device;
+  uint64_t* serve_records;  // device, made on first use by a batched append
+  uint64_t serve_slots;
+  std::mutex serve_mu;
 };
 
 struct gga_array {
@@ -120,6 +124,8 @@ int pool_make(uint64_t bytes, void* slab, uint64_t min_bucket_bytes, uint64_t lf
   pl->slab = slab;
   pl->rings = nullptr;
   pl->state = nullptr;
+  pl->serve_records = nullptr;
+  pl->serve_slots = 0;
   if (cudaGetDevice(&pl->device) != cudaSuccess) {
     delete pl;
     return GGA_ERR_CUDA;
@@ -168,6 +174,7 @@ int pool_free(gga_pool_t* pl) {
   if (pl->state && cudaFree(pl->state) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (pl->rings && cudaFree(pl->rings) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (pl->own_slab && pl->slab && cudaFree(pl->slab) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (pl->serve_records && cudaFree(pl->serve_records) != cudaSuccess) rc = GGA_ERR_CUDA;
   delete pl;
   return rc;
 }
@@ -202,6 +209,21 @@ int sync_status(gga_array* h, cudaStream_t st, bool clear) {
 namespace gga {
 ArrayView* handle_dview(gga_handle h) { return h ? h->dview : nullptr; }
 PoolState* handle_pool(gga_handle h) { return h ? h->pool->state : nullptr; }
+
+// Reservation records of batched appends on the handle's pool: 2 * slots
+// uint64 (first index, then count, per (request, LFVector)), allocated once.
+uint64_t* handle_serve_records(gga_handle h, uint64_t slots) {
+  if (!h) return nullptr;
+  gga_pool_t* pl = h->pool;
+  std::lock_guard<std::mutex> lock(pl->serve_mu);
+  if (pl->serve_records && pl->serve_slots >= slots) return pl->serve_records;
+  if (pl->serve_records) return nullptr;
+  void* p = nullptr;
+  if (cudaMalloc(&p, 2 * slots * sizeof(uint64_t)) != cudaSuccess) return nullptr;
+  pl->serve_records = static_cast<uint64_t*>(p);
+  pl->serve_slots = slots;
+  return pl->serve_records;
+}
 
 bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device, int* num_sms) {
   if (!h) return false;

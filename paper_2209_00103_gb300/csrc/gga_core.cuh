@@ -350,6 +350,7 @@ int launch_twophase_work(void* records, uint64_t n, uint32_t passes, int num_sms
 bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device, int* num_sms);
 ArrayView* handle_dview(gga_handle h);
 PoolState* handle_pool(gga_handle h);
+uint64_t* handle_serve_records(gga_handle h, uint64_t slots);
 uint64_t count_tiles(uint64_t n_rows, uint32_t T, bool vec_ok);
 
 }  // namespace gga

@@ -14,10 +14,12 @@ them into one append launch, one read launch and the flattens of the step
 order), and keeps a few steps in flight; a request completes when its
 step's event has completed.  Appends are admitted by the pool's free
 memory, computed by a host mirror of the device allocator (the same
-per-size free counts and bump pointer, so an admitted append always fits);
-an append that does not fit waits, first come first served within its
-array, and is rejected after a deadline.  The plain mode runs the same
-trace one request at a time, waiting for each.
+per-size free counts and bump pointer, so an admitted append always fits).
+An append that does not fit leaves the ready queue for a waiting queue: it
+is tried again, oldest first, after a flatten has returned memory, and is
+rejected after a deadline.  Its array's later requests stay behind it (per
+array, requests run in arrival order), while other arrays' requests go on.
+The plain mode runs the same trace one request at a time, waiting for each.
 """
 
 from __future__ import annotations
@@ -48,7 +50,7 @@ class ServeConfig:
     mix: tuple = (0.70, 0.25, 0.05)
     read_n: int = 4096
     max_append: int = 1_000_000
-    deadline: float = 1.0
+    deadline: float = 0.05
     seed: int = 4
     max_inflight: int = 3
     max_batch: int = 480
@@ -86,28 +88,35 @@ class PoolMirror:
     def cls(nbytes: int) -> int:
         return max(8, (max(nbytes, 256) - 1).bit_length())
 
-    def need(self, classes):
-        """Bump bytes an allocation of these classes would take now."""
-        bump = 0
-        used = {}
+    @staticmethod
+    def tally(classes):
+        """{class: number of buckets} of a list of bucket classes."""
+        out = {}
         for c in classes:
-            u = used.get(c, 0)
-            if self.free[c] > u:
-                used[c] = u + 1
-            else:
-                bump += 1 << c
+            out[c] = out.get(c, 0) + 1
+        return out
+
+    def need(self, tally):
+        """Bump bytes an allocation of these buckets would take now (free
+        buckets of a class are used first, as the device allocator does)."""
+        bump = 0
+        for c, k in tally.items():
+            f = self.free[c]
+            if k > f:
+                bump += (k - f) << c
         return bump
 
-    def take(self, classes):
-        for c in classes:
-            if self.free[c] > 0:
-                self.free[c] -= 1
-            else:
-                self.bump += 1 << c
+    def take(self, tally):
+        for c, k in tally.items():
+            f = self.free[c]
+            if k > f:
+                self.bump += (k - f) << c
+                f = k
+            self.free[c] = f - k
 
-    def give(self, classes):
-        for c in classes:
-            self.free[c] += 1
+    def give(self, tally):
+        for c, k in tally.items():
+            self.free[c] += k
 
 
 def buckets_for(size: int, B: int) -> int:
@@ -126,21 +135,39 @@ class ArrayState:
         self.busy = False
 
 
-class Server:
-    def __init__(self, cfg: ServeConfig, stream=None, record: bool = False):
+class CudaBackend:
+    """Device side of the server: the library, one stream, events, int64 buffers."""
+
+    def __init__(self):
         import torch
         from . import gga
-        self.gga = gga
         self.torch = torch
+        self.gga = gga
+
+    def stream(self):
+        return self.torch.cuda.Stream()
+
+    def event(self):
+        return self.torch.cuda.Event()
+
+    def empty_i64(self, shape):
+        return self.torch.empty(shape, dtype=self.torch.int64, device="cuda")
+
+
+class Server:
+    LOOK_AHEAD = 32     # waiting appends tried per step after memory was freed
+
+    def __init__(self, cfg: ServeConfig, stream=None, record: bool = False, backend=None):
+        self.be = backend or CudaBackend()
+        gga = self.gga = self.be.gga
         self.cfg = cfg
-        self.stream = stream or torch.cuda.Stream()
+        self.stream = stream or self.be.stream()
         self.pool = gga.GGAPool(cfg.pool_bytes, cfg.B * cfg.E, stream=self.stream)
         self.mirror = PoolMirror(cfg.pool_bytes)
         self.arrays = [ArrayState(gga.GGArray(cfg.L, cfg.T, cfg.B, cfg.E, shared_pool=self.pool,
                                               stream=self.stream), cfg.L) for _ in range(cfg.n_arrays)]
-        self.read_out = torch.empty((cfg.max_inflight + 1, cfg.max_batch, cfg.read_n), dtype=torch.int64,
-                                    device="cuda")
-        self.flat_arena = torch.empty(cfg.flatten_arena_bytes // 8, dtype=torch.int64, device="cuda")
+        self.read_out = self.be.empty_i64((cfg.max_inflight + 1, cfg.max_batch, cfg.read_n))
+        self.flat_arena = self.be.empty_i64(cfg.flatten_arena_bytes // 8)
         self.record = record
         self.results = {}
 
@@ -153,27 +180,41 @@ class Server:
             s = st.sizes[l]
             for b in range(buckets_for(s, cfg.B), buckets_for(s + c, cfg.B)):
                 out.append(PoolMirror.cls((cfg.B << b) * cfg.E))
-        return out
+        return PoolMirror.tally(out)
 
     def _all_classes(self, st: ArrayState):
         cfg = self.cfg
-        return [PoolMirror.cls((cfg.B << b) * cfg.E) for s in st.sizes for b in range(buckets_for(s, cfg.B))]
+        return PoolMirror.tally([PoolMirror.cls((cfg.B << b) * cfg.E) for s in st.sizes
+                                 for b in range(buckets_for(s, cfg.B))])
 
     # -- the loop -----------------------------------------------------------
     def run(self, trace, batched: bool = True):
-        torch = self.torch
         cfg = self.cfg
         t_arr, typ, arr, nn, tag = trace
         m = len(t_arr)
         lat = np.full(m, np.nan)
         state = np.zeros(m, dtype=np.int8)          # 0 pending, 1 done, 2 rejected
-        heap = []                                   # (arrival, request) of array heads ready to be looked at
+        heap = []                                   # (arrival, request): array heads ready to run
+        waiting = []                                # (arrival, request): heads that are appends not fitting yet
+        wait_cls = {}                               # their bucket classes (fixed while they wait)
+        freed = 0                                   # counts frees of pool memory (flattens)
+        checked = 0                                 # value of `freed` when `waiting` was last tried
         nxt = 0
         inflight = deque()                          # (event, [requests], result locations, slot)
         slot = 0
         appended = 0
+        steps = batched_reqs = 0
         max_batch = cfg.max_batch if batched else 1
         t0 = time.perf_counter()
+
+        def next_head(st):
+            st.queue.popleft()
+            if st.queue:
+                heapq.heappush(heap, (t_arr[st.queue[0]], st.queue[0]))
+
+        def fits(cls):
+            return self.mirror.bump + self.mirror.need(cls) <= self.mirror.cap
+
         while True:
             now = time.perf_counter() - t0
             # Arrivals: queue per array; a request becomes a ready head when its array has nothing ahead.
@@ -193,60 +234,84 @@ class Server:
                     state[r] = 1
                     st = self.arrays[arr[r]]
                     st.busy = False
-                    st.queue.popleft()
-                    if st.queue:
-                        heapq.heappush(heap, (t_arr[st.queue[0]], st.queue[0]))
+                    next_head(st)
                     if self.record and r in meta:
                         self._save(r, meta[r])
-            # Build a step from the ready heads, oldest first.
-            appends, reads, flats, blocked, taken = [], [], [], [], []
-            looked = 0
-            while heap and len(taken) < max_batch and looked < 4 * cfg.max_batch:
+            # Appends past their deadline are rejected; their arrays move on.
+            while waiting and now - waiting[0][0] > cfg.deadline:
+                _, r = heapq.heappop(waiting)
+                del wait_cls[r]
+                state[r] = 2
+                next_head(self.arrays[arr[r]])
+            appends, reads, flats, taken = [], [], [], []
+
+            def admit(r, cls):
+                st = self.arrays[arr[r]]
+                self.mirror.take(cls)
+                n = int(nn[r])
+                for l in range(cfg.L):
+                    st.sizes[l] += n // cfg.L + (1 if l < n % cfg.L else 0)
+                appends.append(r)
+                st.busy = True
+                taken.append(r)
+
+            # Waiting appends, oldest first, once memory has been freed since they were last tried.
+            if waiting and freed != checked:
+                checked = freed
+                keep = []
+                tried = 0
+                while waiting and len(taken) < max_batch and tried < self.LOOK_AHEAD:
+                    item = heapq.heappop(waiting)
+                    tried += 1
+                    if fits(wait_cls[item[1]]):
+                        admit(item[1], wait_cls.pop(item[1]))
+                    else:
+                        keep.append(item)
+                for item in keep:
+                    heapq.heappush(waiting, item)
+            # Ready heads, oldest first; an append that does not fit goes to the waiting queue.
+            while heap and len(taken) < max_batch:
                 _, r = heapq.heappop(heap)
-                looked += 1
                 st = self.arrays[arr[r]]
                 if typ[r] == APPEND:
                     cls = self._append_classes(st, int(nn[r]))
-                    if self.mirror.bump + self.mirror.need(cls) <= self.mirror.cap:
-                        self.mirror.take(cls)
-                        for l in range(cfg.L):
-                            st.sizes[l] += int(nn[r]) // cfg.L + (1 if l < int(nn[r]) % cfg.L else 0)
-                        appends.append(r)
-                    elif now - t_arr[r] > cfg.deadline:
-                        state[r] = 2
-                        st.queue.popleft()
-                        if st.queue:
-                            heapq.heappush(heap, (t_arr[st.queue[0]], st.queue[0]))
-                        continue
+                    if fits(cls):
+                        admit(r, cls)
                     else:
-                        blocked.append(r)
-                        continue
-                elif typ[r] == READ:
+                        wait_cls[r] = cls
+                        heapq.heappush(waiting, (t_arr[r], r))
+                    continue
+                if typ[r] == READ:
                     reads.append(r)
                 else:
                     flats.append(r)
                 st.busy = True
                 taken.append(r)
-            for r in blocked:
-                heapq.heappush(heap, (t_arr[r], r))
             if taken:
                 s = self.stream
                 meta = self._launch(appends, reads, flats, arr, nn, tag, slot, s)
+                steps += 1
+                batched_reqs += len(taken)
+                freed += len(flats)
                 appended += int(sum(int(nn[r]) for r in appends))
-                ev = torch.cuda.Event()
+                ev = self.be.event()
                 ev.record(s)
                 inflight.append((ev, taken, meta, slot))
                 slot = (slot + 1) % (cfg.max_inflight + 1)
                 if not batched:
                     ev.synchronize()
             elif not inflight:
-                if nxt >= m and not heap:
+                if nxt >= m and not heap and not waiting:
                     break
                 wait = (t_arr[nxt] - (time.perf_counter() - t0)) if nxt < m else 0.0005
                 if wait > 0:
                     time.sleep(min(wait, 0.0005))
         wall = time.perf_counter() - t0
-        return self._report(lat, state, typ, nn, wall, appended)
+        self.latency, self.state = lat, state
+        rep = self._report(lat, state, typ, nn, wall, appended)
+        rep["steps"] = steps
+        rep["mean_requests_per_step"] = round(batched_reqs / max(1, steps), 3)
+        return rep
 
     def _launch(self, appends, reads, flats, arr, nn, tag, slot, s):
         """Enqueue one step; returns where each read/flatten result lands."""
@@ -278,7 +343,7 @@ class Server:
     def _arena_take(self, n):
         cap = self.flat_arena.shape[0]
         if n + 1 > cap:
-            return self.torch.empty(n + 1, dtype=self.torch.int64, device="cuda")
+            return self.be.empty_i64(n + 1)
         if self._arena_ptr + n + 1 > cap:
             self._arena_ptr = 0
         dst = self.flat_arena[self._arena_ptr:self._arena_ptr + n + 1]

@@ -47,6 +47,25 @@ def test_append_and_read_batches_match_oracle():
     pool.close()
 
 
+def test_append_batch_over_many_lfvectors_splits_launches():
+    # 12 arrays of 1024 LFVectors: more (request, LFVector) pairs than one
+    # launch's reservation records, so the batch runs as several launches.
+    pool = gga.GGAPool(256 << 20, 256 * 4)
+    shapes = [(1024, 32, 256, (4, 8, 16)[a % 3]) for a in range(12)]
+    arrays = [gga.GGArray(L, T, B, E, shared_pool=pool) for (L, T, B, E) in shapes]
+    refs = [oracle.OracleGGArray(L, T, B, E) for (L, T, B, E) in shapes]
+    for step, ns in enumerate([[3000 + 977 * a for a in range(12)], [1024 * 40 + 5] * 12, [1, 0, 2047] * 4]):
+        gga.gga_append_batch([(g, n, 100 * step + a + 1) for a, (g, n) in enumerate(zip(arrays, ns))])
+        for a, (o, n) in enumerate(zip(refs, ns)):
+            o.append(n, 100 * step + a + 1)
+    for g, o in zip(arrays, refs):
+        assert_same_state(g, o)
+        assert g.last_error() == gga.GGA_OK
+    for g in arrays:
+        g.close()
+    pool.close()
+
+
 def small_cfg(**kw):
     base = dict(n_arrays=64, L=4, T=256, B=1024, E=8, pool_bytes=2 << 30, rate=20000.0, duration=0.25,
                 max_append=50000, deadline=1.0, max_inflight=3, max_batch=480, flatten_arena_bytes=1 << 30)
