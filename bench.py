@@ -606,12 +606,15 @@ def run_two_phase(args, world, rank, local):
     g = gga.GGArray(w.L, w.T, w.B, 16, pool_bytes)
     born = torch.zeros(w.L, dtype=torch.int64, device=dev) if w.only_newborn else None
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(w.generations + 4)]
+    offs = torch.zeros((w.generations + 1, w.L + 1), dtype=torch.int64, device=dev)
     ev[0].record(stream)
     g.insert(counts, recs, stream)
     ev[1].record(stream)
+    gga.gga_offsets(g.h, offs[0], stream)
     for gen in range(w.generations):
         gga.gga_twophase_spawn(g.h, gen, w.seed, born, stream)
         ev[2 + gen].record(stream)
+        gga.gga_offsets(g.h, offs[gen + 1], stream)   # sizes after the generation (8 KB copy, outside the events)
     n, rc = g.size(stream)
     if rc != gga.GGA_OK:
         raise RuntimeError(f"device error {rc}")
@@ -627,6 +630,14 @@ def run_two_phase(args, world, rank, local):
     c.record(stream)
     torch.cuda.synchronize(dev)
     spawn_ms = ev[1].elapsed_time(ev[1 + w.generations])
+    sizes = [int(x) for x in offs[:, w.L].cpu()]
+    # Algorithmic bytes of the spawning: every parent record read (16 B), every child written (16 B).
+    # All records spawn in reading A; in reading B only the previous generation's newborns do.
+    spawn_bytes = 0
+    for k in range(w.generations):
+        parents = sizes[k] if not w.only_newborn else (sizes[k] - (sizes[k - 1] if k else 0))
+        spawn_bytes += 16 * parents + 16 * (sizes[k + 1] - sizes[k])
+    spawn_gen_ms = [ev[1 + k].elapsed_time(ev[2 + k]) for k in range(w.generations)]
     flat_ms = a.elapsed_time(b)
     work_ms = b.elapsed_time(c)
     peak, _ = peaks()
@@ -640,12 +651,16 @@ def run_two_phase(args, world, rank, local):
                       "final_records": n, "spawning": "newborn" if w.only_newborn else "all records",
                       "passes": w.passes},
            "phases_ms": {"initial_insert": round(ev[0].elapsed_time(ev[1]), 3),
-                         "spawn_generations": [round(ev[1 + k].elapsed_time(ev[2 + k]), 3) for k in range(w.generations)],
+                         "spawn_generations": [round(x, 3) for x in spawn_gen_ms],
                          "flatten": round(flat_ms, 3), "work_passes": round(work_ms, 3)},
            "flatten_gbs": round(2 * n * 16 / (flat_ms / 1e3) / 1e9, 1),
            "flatten_frac_of_measured_peak": round(2 * n * 16 / (flat_ms / 1e3) / 1e9 / peak, 3),
            "work_pass_gbs_aos": round(w.passes * 32 * n / (work_ms / 1e3) / 1e9, 1),
-           "spawn_gbs": round((spawned * 16 + (n - spawned) * 16) / (spawn_ms / 1e3) / 1e9, 1),
+           "records_after_generation": sizes,
+           "spawn_gbs": round(spawn_bytes / (spawn_ms / 1e3) / 1e9, 1),
+           "spawn_frac_of_measured_peak": round(spawn_bytes / (spawn_ms / 1e3) / 1e9 / peak, 3),
+           "last_generation_gbs": round((16 * (sizes[-2] if not w.only_newborn else sizes[-2] - sizes[-3])
+                                         + 16 * (sizes[-1] - sizes[-2])) / (spawn_gen_ms[-1] / 1e3) / 1e9, 1),
            "mem_over_needed": round(mem["bucket_bytes"] / max(1, mem["live_bytes"]), 4)}
     g.close()
     return res

@@ -339,9 +339,13 @@ int gga_batch_destroy(gga_batch b);
  * Request batches for serving many live arrays (continuous batching: the
  * requests that arrived while earlier work ran are launched together).
  *
- * gga_append_batch -- append reqs[i].n elements to reqs[i].array for all i,
- * in one launch (one block per (request, LFVector): one reservation, the
- * buckets it reaches from the pool, then the writes).  Every LFVector l of
+ * gga_append_batch -- append reqs[i].n elements to reqs[i].array for all i.
+ * One kernel reserves every (request, LFVector) share (one size update, the
+ * buckets it reaches from the pool: Algorithm 1 and 2) and recomputes each
+ * array's offsets; a second kernel writes the elements, 16K elements per
+ * block.  Requests are launched in groups of at most 480 requests and 8192
+ * (request, LFVector) pairs; the first call on a pool allocates that pool's
+ * 128 KB of reservation records (kept until gga_pool_destroy).  Every LFVector l of
  * the array gets n / L elements, one more for the first n % L; element k
  * appended to LFVector l has the value tag * 2^24 + l * 2^20 + k (stored as
  * E bytes like gga_insert_generated's values), so n / L must be below 2^20.
