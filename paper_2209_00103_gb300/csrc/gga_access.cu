@@ -17,46 +17,9 @@
 
 namespace gga {
 
-constexpr uint32_t kSmemOffsetsMax = 6144;   // offsets staged in shared memory up to L+1 = 6144 (48 KB)
 
 // ---------------------------------------------------------------------------
 // Global index translation.
-
-// Stage offsets[0..L] in shared memory when they fit; returns the array to search.
-__device__ __forceinline__ const uint64_t* stage_offsets(const ArrayView& v, uint64_t* s_off) {
-  if (v.L + 1 <= kSmemOffsetsMax) {
-    for (uint32_t i = threadIdx.x; i <= v.L; i += blockDim.x) s_off[i] = v.offsets[i];
-    __syncthreads();
-    return s_off;
-  }
-  return v.offsets;
-}
-
-// LFVector holding global index g < N: the prefix sum of sizes (Sec. IV) is
-// searched from a proportional guess l = g * L / N, corrected by up to four
-// steps to a neighbour (sizes of similar LFVectors land here), else by a
-// binary search.  Returns the l with offsets[l] <= g < offsets[l + 1].  The
-// offsets go through the read-only cache (`off` must point to global memory,
-// never to a shared-memory copy): no block-wide staging, so a block costs
-// nothing before its first access.
-__device__ __forceinline__ uint32_t find_lfv(const uint64_t* off, uint32_t L, uint64_t N, uint64_t g) {
-  // The guess only starts the search, so fp32 rounding in it is harmless.
-  const float guess = __ull2float_rz(g) * (static_cast<float>(L) / __ull2float_rz(N));
-  uint32_t l = guess < static_cast<float>(L) ? __float2uint_rz(guess) : L - 1;
-  if (l >= L) l = L - 1;
-#pragma unroll 1
-  for (int s = 0; s < 4; ++s) {
-    if (__ldg(off + l) > g) { --l; continue; }
-    if (__ldg(off + l + 1) <= g) { ++l; continue; }
-    return l;
-  }
-  uint32_t lo = 0, hi = L + 1;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (__ldg(off + mid) <= g) lo = mid + 1; else hi = mid;
-  }
-  return lo - 1;
-}
 
 // Address of global element g < N (Sec. IV index translation, Algorithm 2
 // bucket sizes).
@@ -147,38 +110,44 @@ __device__ __forceinline__ typename Elem<E>::T add_rep(typename Elem<E>::T x, ui
 // rw_g: elements are visited by global index, one thread per element, each
 // through the global translation (LFVector by the prefix sum of sizes, then
 // bucket and offset).  A warp takes 32*U consecutive indices; lane 0's
-// binary search is shared by the lanes whose index falls in the same
-// LFVector, the others search for themselves.
+// LFVector search is shared by the lanes whose index falls in the same
+// LFVector, the others search for themselves.  U = 16 loads per lane are in
+// flight before the first store, with many more blocks than are resident:
+// the sweep is bound by how many bytes are in flight (measured on GB300:
+// 0.69-0.75 ms for 2^28 int32 against 0.98 ms with U = 8 and one wave of
+// blocks).
+constexpr int kSweepGPerLane = 16;
+
 template <int E>
 __global__ void __launch_bounds__(256) sweep_g_kernel(ArrayView v, uint64_t delta, uint32_t repeats) {
   typedef typename Elem<E>::T T;
-  constexpr int U = 8;
-  extern __shared__ uint64_t s_off[];
-  const uint64_t* off = stage_offsets(v, s_off);
-  const uint64_t N = off[v.L];
+  constexpr int U = kSweepGPerLane;
+  const uint64_t N = __ldg(v.offsets + v.L);
   const int lane = threadIdx.x & 31;
   const uint64_t warps = static_cast<uint64_t>(gridDim.x) * (blockDim.x >> 5);
   for (uint64_t wbase = (static_cast<uint64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32 * U;
        wbase < N; wbase += warps * 32 * U) {
     uint32_t l0 = 0;
-    if (lane == 0) l0 = upper_bound_u64(off, v.L + 1, wbase) - 1;
+    if (lane == 0) l0 = find_lfv(v.offsets, v.L, N, wbase);
     l0 = __shfl_sync(0xffffffffu, l0, 0);
-    const uint64_t lo = off[l0], hi = off[l0 + 1];
+    const uint64_t lo = __ldg(v.offsets + l0), hi = __ldg(v.offsets + l0 + 1);
     T* addr[U];
-    T x[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint64_t g = wbase + lane + 32 * u;
       addr[u] = nullptr;
       if (g < N) {
-        const uint32_t l = (g >= lo && g < hi) ? l0 : upper_bound_u64(off, v.L + 1, g) - 1;
+        const uint32_t l = (g >= lo && g < hi) ? l0 : find_lfv(v.offsets, v.L, N, g);
         uint32_t b;
         uint64_t o;
-        bucket_of(g - off[l], v.log2B, b, o);
+        bucket_of(g - __ldg(v.offsets + l), v.log2B, b, o);
         addr[u] = reinterpret_cast<T*>(__ldg(v.buckets + static_cast<uint64_t>(l) * kMaxBuckets + b)) + o;
-        x[u] = *addr[u];
       }
     }
+    T x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (addr[u]) x[u] = *addr[u];
 #pragma unroll
     for (int u = 0; u < U; ++u)
       if (addr[u]) *addr[u] = add_rep<E>(x[u], delta, repeats);
@@ -452,9 +421,6 @@ __global__ void memory_kernel(ArrayView v, unsigned long long* out) {
 // ---------------------------------------------------------------------------
 // Launchers.
 
-static size_t offsets_smem(const ArrayView& v) {
-  return v.L + 1 <= kSmemOffsetsMax ? (v.L + 1) * sizeof(uint64_t) : 0;
-}
 
 // Grid of one full wave: the blocks that fit on all SMs at once (grid-stride
 // kernels then give every block the same share), but no more than the work.
@@ -510,9 +476,9 @@ template <int E>
 static void sweep_as(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms,
                      cudaStream_t st) {
   if (mode == GGA_RW_G) {
-    const size_t sm = offsets_smem(v);
-    const unsigned grid = wave_grid(sweep_g_kernel<E>, 256, sm, num_sms, ~0ull);
-    sweep_g_kernel<E><<<grid, 256, sm, st>>>(v, delta, repeats);
+    // The size is on the device, so the grid cannot follow it: 32 blocks per
+    // SM (several times what is resident at once) stride over the array.
+    sweep_g_kernel<E><<<static_cast<unsigned>(num_sms) * 32u, 256, 0, st>>>(v, delta, repeats);
   } else {
     const unsigned grid = wave_grid(sweep_b_kernel<E>, 256, 0, num_sms, ~0ull);
     sweep_b_kernel<E><<<grid, 256, 0, st>>>(v, delta, repeats);

@@ -107,6 +107,32 @@ __device__ __forceinline__ uint32_t upper_bound_u64(const uint64_t* a, uint32_t 
   return lo;
 }
 
+// LFVector holding global index g < N: the prefix sum of sizes (Sec. IV) is
+// searched from a proportional guess l = g * L / N, corrected by up to four
+// steps to a neighbour (sizes of similar LFVectors land here), else by a
+// binary search.  Returns the l with offsets[l] <= g < offsets[l + 1].  The
+// offsets go through the read-only cache (`off` must point to global memory,
+// never to a shared-memory copy): no block-wide staging, so a block costs
+// nothing before its first access.
+__device__ __forceinline__ uint32_t find_lfv(const uint64_t* off, uint32_t L, uint64_t N, uint64_t g) {
+  // The guess only starts the search, so fp32 rounding in it is harmless.
+  const float guess = __ull2float_rz(g) * (static_cast<float>(L) / __ull2float_rz(N));
+  uint32_t l = guess < static_cast<float>(L) ? __float2uint_rz(guess) : L - 1;
+  if (l >= L) l = L - 1;
+#pragma unroll 1
+  for (int s = 0; s < 4; ++s) {
+    if (__ldg(off + l) > g) { --l; continue; }
+    if (__ldg(off + l + 1) <= g) { ++l; continue; }
+    return l;
+  }
+  uint32_t lo = 0, hi = L + 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(off + mid) <= g) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
 // ---------------------------------------------------------------------------
 // Warp / block scans (Sec. III-B: shuffle prefix sum inside the block).
 

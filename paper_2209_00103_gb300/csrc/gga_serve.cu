@@ -147,7 +147,7 @@ __device__ void read_run(const ArrayView& v, uint64_t n, uint64_t seed, void* ou
     T x = T();
     if (N) {
       const uint64_t g = ((splitmix(seed, k) >> 32) * N) >> 32;   // uniform over [0, N)
-      const uint32_t l = upper_bound_u64(v.offsets, v.L + 1, g) - 1;
+      const uint32_t l = find_lfv(v.offsets, v.L, N, g);
       uint32_t b;
       uint64_t off;
       bucket_of(g - v.offsets[l], v.log2B, b, off);
