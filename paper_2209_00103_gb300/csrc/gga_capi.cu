@@ -48,6 +48,8 @@ struct gga_array {
   gga::InsertScratch ins;   // pointers into meta (fixed part) and scratch (per-call part)
   unsigned long long* memstats;
   gga::ArrayView* dview;    // device copy of `view`, for kernels that take many arrays
+  void* wscratch;           // binned random writes: bins of (address, value), kept between calls
+  size_t wscratch_bytes;
 };
 
 namespace {
@@ -382,7 +384,23 @@ int gga_write(gga_handle h, const uint64_t* idx_dev, uint64_t n, const void* in_
   if (!h || (n > 0 && (!idx_dev || !in_dev))) return GGA_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(in_dev) % h->p.elem_bytes) != 0) return GGA_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(idx_dev) & 7) != 0) return GGA_ERR_INVALID;
-  return gga::launch_write(h->view, idx_dev, n, in_dev, h->num_sms, S(stream));
+  // Large batches go through bins kept in the handle (grown stream-ordered;
+  // if the allocation fails the writes go directly).
+  const size_t need = gga::wbin_scratch_bytes(n, h->p.elem_bytes);
+  if (need > h->wscratch_bytes) {
+    cudaStream_t st = S(stream);
+    if (h->wscratch) cudaFreeAsync(h->wscratch, st);
+    h->wscratch = nullptr;
+    h->wscratch_bytes = 0;
+    if (cudaMallocAsync(&h->wscratch, need, st) == cudaSuccess && cudaMemsetAsync(h->wscratch, 0, 1024, st) == cudaSuccess) {
+      h->wscratch_bytes = need;
+    } else {
+      cudaGetLastError();
+      if (h->wscratch) cudaFreeAsync(h->wscratch, st);
+      h->wscratch = nullptr;
+    }
+  }
+  return gga::launch_write(h->view, idx_dev, n, in_dev, h->num_sms, need ? h->wscratch : nullptr, S(stream));
 }
 
 int gga_sweep(gga_handle h, int mode, uint64_t delta, uint32_t repeats, void* stream) {
@@ -473,6 +491,7 @@ int gga_destroy(gga_handle h) {
   if (!h->own_pool && h->pool && h->meta && gga::launch_clear(h->view, nullptr) != GGA_OK) rc = GGA_ERR_CUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) rc = GGA_ERR_CUDA;
   if (h->scratch && cudaFree(h->scratch) != cudaSuccess) rc = GGA_ERR_CUDA;
+  if (h->wscratch && cudaFree(h->wscratch) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (h->meta && cudaFree(h->meta) != cudaSuccess) rc = GGA_ERR_CUDA;
   if (h->own_pool && h->pool && pool_free(h->pool) != GGA_OK) rc = GGA_ERR_CUDA;
   delete h;

@@ -360,8 +360,11 @@ int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32
                             uint32_t* done_counter, int num_sms, cudaStream_t st);
 int launch_finalize(const ArrayView& v, cudaStream_t st);
 int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st);
-int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms,
+// scratch: nullptr, or wbin_scratch_bytes(n, E) bytes whose first 1 KB is
+// zero before the first call (the binned path for n >= 2^20 keeps it so).
+int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void* in, int num_sms, void* scratch,
                  cudaStream_t st);
+uint64_t wbin_scratch_bytes(uint64_t n, uint32_t E);
 int launch_sweep(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms, cudaStream_t st);
 int launch_flatten(const ArrayView& v, void* dst, uint64_t cap_elems, int num_sms, cudaStream_t st);
 int launch_clear(const ArrayView& v, cudaStream_t st);
