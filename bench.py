@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--rounds", type=int, default=512, help="insertion rounds per step (512 = full workload)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true", help="skip the static / semi-static flat arrays")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase"],
@@ -342,6 +343,11 @@ def run_ours(args, world, rank, local):
     # Insert carries the headline roofline of the growable array itself.
     ins_gbs = ab["insert"] / (ph_ms["insert"] / 1e3) / 1e9
 
+    # The paper's comparison arrays (Sec. II) on the same inputs.
+    baselines = None
+    if not args.no_baselines and rank == 0 and w.E == 4:
+        baselines = run_flat_baselines(counts, values, idx_r, idx_w, vals_w, N, R, w.L, w.T, dev, stream)
+
     # End to end through the C ABI with host buffers.
     e2e = None
     if not args.no_e2e:
@@ -371,11 +377,109 @@ def run_ours(args, world, rank, local):
         "gpu_launches": K * (sum(LAUNCHES_PER_STEP.values()) - (0 if binned else 3)),
         "clocks": clocks,
         "e2e": e2e,
+        "baselines": baselines,
     }
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(R)
     g.close()
     return result
+
+
+def run_flat_baselines(counts, values, idx_r, idx_w, vals_w, N, R, L, T, dev, stream, steps=5):
+    """The comparison arrays of the paper's Sec. II on the same inputs and GPU,
+    as plain flat arrays with PyTorch's own kernels (they are baselines, not
+    part of the GGArray path):
+      static       allocated once for the worst case (every thread inserting 2
+                   elements every round), so no growth ever happens;
+      semi_static  grown from the host by doubling: before each round the
+                   host reads the round's total (one synchronization) and, if
+                   it does not fit, allocates twice the capacity and copies.
+    Values arrive packed in prefix-sum order, so an insertion writes them
+    contiguously after the current size.  A flat array is already
+    contiguous: it needs no flatten.  Both sweeps (rw_b, rw_g) are one +1 pass."""
+    per_round = counts.view(R, -1)
+    out = {}
+
+    def phase_times(run, k):
+        names = ["insert", "read", "write", "rw_b", "rw_g"]
+        res = {n: [] for n in names}
+        for _ in range(k):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+            run(ev)
+            torch.cuda.synchronize(dev)
+            for i, n in enumerate(names):
+                res[n].append(ev[i].elapsed_time(ev[i + 1]))
+        return {n: round(statistics.median(v), 4) for n, v in res.items()}
+
+    read_out = torch.empty_like(idx_r, dtype=values.dtype)
+
+    # Static: worst-case capacity.
+    cap = 2 * R * L * T
+    a = torch.empty(cap, dtype=values.dtype, device=dev)
+
+    def static_step(ev):
+        ev[0].record(stream)
+        total = per_round.sum()                            # the insertion's size update (< 2^31 here)
+        a[:N].copy_(values)
+        ev[1].record(stream)
+        torch.index_select(a[:N], 0, idx_r, out=read_out)
+        ev[2].record(stream)
+        a.index_copy_(0, idx_w, vals_w)
+        ev[3].record(stream)
+        a[:N].add_(1)
+        ev[4].record(stream)
+        a[:N].add_(1)
+        ev[5].record(stream)
+        return total
+
+    phase_times(static_step, 2)
+    ph = phase_times(static_step, steps)
+    ms = sum(ph.values())
+    out["static"] = {"capacity_elems": cap, "mem_over_needed": round(cap / N, 4), "phases_ms": ph,
+                     "flatten_ms": 0.0, "ms_per_step": round(ms, 4), "gelem_s": round(N / (ms / 1e3) / 1e9, 3)}
+    del a
+
+    # Semi-static: host-resized by doubling, checked every round.
+    state = {}
+
+    def semi_step(ev):
+        ev[0].record(stream)
+        c = 1 << 20
+        buf = torch.empty(c, dtype=values.dtype, device=dev)
+        size = 0
+        for r in range(R):
+            n_r = int(per_round[r].sum().item())                   # host learns the round's total
+            if size + n_r > c:
+                while size + n_r > c:
+                    c *= 2
+                nb = torch.empty(c, dtype=values.dtype, device=dev)
+                nb[:size].copy_(buf[:size])
+                buf = nb
+            buf[size:size + n_r].copy_(values[size:size + n_r])
+            size += n_r
+        ev[1].record(stream)
+        torch.index_select(buf[:size], 0, idx_r, out=read_out)
+        ev[2].record(stream)
+        buf.index_copy_(0, idx_w, vals_w)
+        ev[3].record(stream)
+        buf[:size].add_(1)
+        ev[4].record(stream)
+        buf[:size].add_(1)
+        ev[5].record(stream)
+        state["cap"] = c
+        state["size"] = size
+
+    phase_times(semi_step, 1)
+    ph = phase_times(semi_step, max(1, steps // 2))
+    ms = sum(ph.values())
+    out["semi_static"] = {"capacity_elems": state["cap"], "mem_over_needed": round(state["cap"] / N, 4),
+                          "phases_ms": ph, "flatten_ms": 0.0, "host_syncs_per_step": R,
+                          "ms_per_step": round(ms, 4), "gelem_s": round(N / (ms / 1e3) / 1e9, 3)}
+    if state["size"] != N:
+        raise RuntimeError("semi-static baseline inserted a wrong number of elements")
+    out["note"] = ("flat arrays with PyTorch kernels (index_select / index_copy_ / add_); "
+                   "the GGArray's write phase uses its own binned writes")
+    return out
 
 
 def run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world, dev, stream):
