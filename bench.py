@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--no-baselines", action="store_true", help="skip the static / semi-static flat arrays")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase"],
+    ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling"],
                     default="paper_growth",
                     help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch; "
                          "served: continuous-batching request server")
@@ -821,6 +821,115 @@ def run_two_phase(args, world, rank, local):
     return res
 
 
+def run_doubling(args, world, rank, local):
+    """The growable-array experiment of the paper's Sec. VI-C (Table II):
+    start at 10^6 int32 elements and double the size 10 times (to 1.024e9).
+    Every doubling is a resize (capacity raised to twice the size: gga_reserve
+    for a GGArray), an insertion of one element per element already there
+    (gga_insert of one round: each LFVector's share split over its 1024
+    threads, values packed in prefix-sum order), and a read/write pass adding
+    +1 thirty times to every element (rw_b, the paper's per-block r/w).
+    GGArray with 32 and 512 LFVectors (first bucket 4096) and a static array
+    allocated for the last size up front (no grow; contiguous copy for the
+    insertion, +30 in one pass with PyTorch)."""
+    import numpy as np
+    from paper_2209_00103_gb300 import gga
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    T, B, E = 1024, 4096, 4
+    n0, iters = 1_000_000, 10
+    final = n0 << iters
+    values = torch.arange(final // 2, dtype=torch.int32, device=dev)     # the largest insertion's values
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def split(n, parts):
+        return np.array([n // parts + (1 if i < n % parts else 0) for i in range(parts)], dtype=np.int64)
+
+    rows = {}
+    for L in (32, 512):
+        g = gga.GGArray(L, T, B, E, int(2.3 * final * E) + L * B * E * 4)
+        sizes = np.zeros(L, dtype=np.int64)
+        per_iter = []
+
+        def insert_counts(add):
+            c = np.zeros((1, L, T), dtype=np.uint32)
+            for l in range(L):
+                c[0, l, :] = split(int(add[l]), T)
+            return torch.from_numpy(c.view(np.int32)).to(dev)
+
+        # The initial 10^6 elements.
+        add = split(n0, L)
+        g.insert(insert_counts(add), values[:n0], stream)
+        sizes += add
+        for it in range(iters):
+            target = torch.from_numpy((2 * sizes).astype(np.int64)).to(dev)
+            counts = insert_counts(sizes)
+            n_add = int(sizes.sum())
+            torch.cuda.synchronize(dev)
+            e = [ev() for _ in range(4)]
+            e[0].record(stream)
+            g.reserve(target, stream)
+            e[1].record(stream)
+            g.insert(counts, values[:n_add], stream)
+            e[2].record(stream)
+            g.sweep(gga.GGA_RW_B, 1, 30, stream)
+            e[3].record(stream)
+            torch.cuda.synchronize(dev)
+            sizes = 2 * sizes
+            per_iter.append({"size_after": int(sizes.sum()), "grow_ms": round(e[0].elapsed_time(e[1]), 4),
+                             "insert_ms": round(e[1].elapsed_time(e[2]), 4), "rw_ms": round(e[2].elapsed_time(e[3]), 4)})
+        n, rc = g.size(stream)
+        if rc != gga.GGA_OK or n != final:
+            raise RuntimeError(f"doubling GGArray{L}: size {n} vs {final}, device error {rc}")
+        mem = g.memory(stream)
+        rows[f"GGArray{L}"] = {"last": per_iter[-1], "iterations": per_iter,
+                               "mem_over_needed": round(mem["bucket_bytes"] / max(1, mem["live_bytes"]), 4)}
+        g.close()
+
+    # Static: allocated for the last size; insertion is a contiguous copy after the size.
+    a = torch.zeros(final, dtype=torch.int32, device=dev)
+    size = n0
+    a[:n0].copy_(values[:n0])
+    per_iter = []
+    for it in range(iters):
+        torch.cuda.synchronize(dev)
+        e = [ev() for _ in range(3)]
+        e[0].record(stream)
+        a[size:2 * size].copy_(values[:size])
+        e[1].record(stream)
+        a[:2 * size].add_(30)
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        size *= 2
+        per_iter.append({"size_after": size, "grow_ms": None, "insert_ms": round(e[0].elapsed_time(e[1]), 4),
+                         "rw_ms": round(e[1].elapsed_time(e[2]), 4)})
+    rows["static"] = {"last": per_iter[-1], "iterations": per_iter, "mem_over_needed": 1.0}
+    del a
+
+    last512 = rows["GGArray512"]["last"]
+    peak, _ = peaks()
+    ins_bytes = (final // 2) * 2 * E + 512 * T * 4          # values read + elements written + counts
+    rw_bytes = final * 2 * E
+    return {"metric": "growable-array doubling (Sec. VI-C, Table II): last doubling 5.12e8 -> 1.024e9 int32",
+            "value": round((final // 2) / (last512["insert_ms"] / 1e3) / 1e9, 3), "unit": "Gelem/s (GGArray512 insert)",
+            "n_gpus": world, "steps": iters, "warmup": 0, "ms_per_step": round(
+                last512["grow_ms"] + last512["insert_ms"] + last512["rw_ms"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "doubling_1e6_x2_10_int32", "T": T, "B": B, "start": n0, "final": final},
+            "roofline": {"bound": "hbm", "kernel": "GGArray512 insertion (count + tile scan + reserve + copy)",
+                         "achieved": round(ins_bytes / (last512["insert_ms"] / 1e3) / 1e9, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(ins_bytes / (last512["insert_ms"] / 1e3) / 1e9 / peak, 3),
+                         "traffic": None},
+            "rw_gbs_GGArray512": round(rw_bytes / (last512["rw_ms"] / 1e3) / 1e9, 1),
+            "table": rows,
+            "paper_table_ii_a100_ms": {"static": {"grow": None, "insert": 7.07, "rw": 6.27},
+                                       "memMap": {"grow": 5.21, "insert": 7.87, "rw": 6.28},
+                                       "GGArray512": {"grow": 8.76, "insert": 11.79, "rw": 69.73},
+                                       "GGArray32": {"grow": 0.52, "insert": 27.90, "rw": 198.32}}}
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -832,6 +941,8 @@ def main():
         res = run_served(args, world, rank, local)
     elif args.workload == "two_phase":
         res = run_two_phase(args, world, rank, local)
+    elif args.workload == "doubling":
+        res = run_doubling(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -198,6 +198,19 @@ int gga_insert_noalloc(gga_handle h, const uint32_t* counts_dev, uint32_t rounds
                        const void* values_dev, uint64_t n_values, void* stream);
 
 /*
+ * gga_reserve -- resize without inserting (the "grow" step of the paper's
+ * growable-array experiment, Sec. VI-C / Table II: capacity is raised when
+ * necessary before an insertion).  target_dev: device, L uint64 (8-byte
+ * aligned); afterwards LFVector l's capacity is at least target_dev[l]
+ * elements: the buckets that capacity reaches are taken from the pool
+ * (Algorithm 2), as an insertion of that many elements would take them.
+ * Sizes and contents do not change; capacity never shrinks.  An LFVector
+ * whose buckets do not fit keeps the longest prefix that did and
+ * GGA_ERR_POOL_EXHAUSTED is latched.
+ */
+int gga_reserve(gga_handle h, const uint64_t* target_dev, void* stream);
+
+/*
  * gga_insert_generated -- the same insertion with counts and values drawn
  * inside the inserting threads (spec above), as a kernel calling push_back
  * does.  spec is a host pointer.  Device errors as gga_insert.

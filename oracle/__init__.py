@@ -66,6 +66,8 @@ def _load():
         lib.orc_size.argtypes = [ctypes.c_void_p]
         lib.orc_sizes.argtypes = [ctypes.c_void_p, u8p]
         lib.orc_capacities.argtypes = [ctypes.c_void_p, u8p, u8p]
+        lib.orc_reserve.restype = ctypes.c_int
+        lib.orc_reserve.argtypes = [ctypes.c_void_p, u8p]
         lib.orc_offsets.argtypes = [ctypes.c_void_p, u8p]
         lib.orc_bucket_of.argtypes = [ctypes.c_uint64, ctypes.c_uint64,
                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]
@@ -192,6 +194,12 @@ class OracleGGArray:
         out = np.zeros(self.L, dtype=np.uint64)
         self._lib.orc_sizes(self._h, _ptr(out))
         return out
+
+    def reserve(self, target) -> int:
+        """Resize: capacity of LFVector l at least target[l] (see orc_reserve)."""
+        t = np.ascontiguousarray(target, dtype=np.uint64)
+        assert t.shape == (self.L,)
+        return self._lib.orc_reserve(self._h, _ptr(t))
 
     def capacities(self):
         caps = np.zeros(self.L, dtype=np.uint64)

@@ -61,6 +61,8 @@ struct OracleArray {
   // lfv[l] holds LFVector l's elements back to back, E bytes each, in
   // insertion order.
   std::vector<std::vector<unsigned char>> lfv;
+  // reserved[l]: the largest capacity asked for by a resize (0 if none).
+  std::vector<uint64_t> reserved;
 };
 
 bool is_power_of_two(uint64_t x) { return x != 0 && (x & (x - 1)) == 0; }
@@ -205,6 +207,7 @@ void* orc_create(uint32_t L, uint32_t T, uint64_t B, uint32_t E) {
   a->B = B;
   a->E = E;
   a->lfv.assign(L, {});
+  a->reserved.assign(L, 0);
   return a;
 }
 
@@ -346,13 +349,30 @@ void orc_sizes(void* h, uint64_t* out) {
   for (uint32_t l = 0; l < a.L; ++l) out[l] = lfv_size(a, l);
 }
 
+// Elements LFVector l's buckets must cover: its size, or more if a resize
+// asked for more.
+static uint64_t covered(const OracleArray& a, uint32_t l) {
+  const uint64_t s = lfv_size(a, l);
+  return s > a.reserved[l] ? s : a.reserved[l];
+}
+
 // Capacity and bucket count of every LFVector under lazy bucket allocation.
 void orc_capacities(void* h, uint64_t* caps, uint64_t* nbuckets) {
   OracleArray& a = *static_cast<OracleArray*>(h);
   for (uint32_t l = 0; l < a.L; ++l) {
-    if (caps) caps[l] = capacity_of(lfv_size(a, l), a.B);
-    if (nbuckets) nbuckets[l] = buckets_of(lfv_size(a, l), a.B);
+    if (caps) caps[l] = capacity_of(covered(a, l), a.B);
+    if (nbuckets) nbuckets[l] = buckets_of(covered(a, l), a.B);
   }
+}
+
+// Resize (the grow step of Sec. VI-C's experiment): LFVector l's buckets
+// are allocated until its capacity is at least target[l]; sizes and
+// contents stay.
+int orc_reserve(void* h, const uint64_t* target) {
+  OracleArray& a = *static_cast<OracleArray*>(h);
+  for (uint32_t l = 0; l < a.L; ++l)
+    if (target[l] > a.reserved[l]) a.reserved[l] = target[l];
+  return ORC_OK;
 }
 
 // Prefix sum of LFVector sizes, L+1 entries (Sec. IV).
@@ -458,7 +478,7 @@ uint64_t orc_lfvector(void* h, uint32_t l, void* out) {
 uint64_t orc_bucket_bytes(void* h) {
   OracleArray& a = *static_cast<OracleArray*>(h);
   uint64_t bytes = 0;
-  for (uint32_t l = 0; l < a.L; ++l) bytes += capacity_of(lfv_size(a, l), a.B) * a.E;
+  for (uint32_t l = 0; l < a.L; ++l) bytes += capacity_of(covered(a, l), a.B) * a.E;
   return bytes;
 }
 

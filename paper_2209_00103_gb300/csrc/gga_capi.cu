@@ -365,6 +365,12 @@ int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds, const 
   return gga::launch_insert(h->view, h->ins, counts_dev, rounds, values_dev, n_values, h->num_sms, st);
 }
 
+int gga_reserve(gga_handle h, const uint64_t* target_dev, void* stream) {
+  if (!h || !target_dev) return GGA_ERR_INVALID;
+  if ((reinterpret_cast<uintptr_t>(target_dev) & 7) != 0) return GGA_ERR_INVALID;
+  return gga::launch_reserve(h->view, target_dev, S(stream));
+}
+
 int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds, void* stream) {
   if (!h || !spec) return GGA_ERR_INVALID;
   if (spec->dist > GGA_DIST_POISSON || spec->n_thresholds > GGA_MAX_THRESHOLDS) return GGA_ERR_INVALID;

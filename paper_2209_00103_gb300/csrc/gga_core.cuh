@@ -367,6 +367,7 @@ int launch_write(const ArrayView& v, const uint64_t* idx, uint64_t n, const void
 uint64_t wbin_scratch_bytes(uint64_t n, uint32_t E);
 int launch_sweep(const ArrayView& v, int mode, uint64_t delta, uint32_t repeats, int num_sms, cudaStream_t st);
 int launch_flatten(const ArrayView& v, void* dst, uint64_t cap_elems, int num_sms, cudaStream_t st);
+int launch_reserve(const ArrayView& v, const uint64_t* target, cudaStream_t st);
 int launch_clear(const ArrayView& v, cudaStream_t st);
 int launch_caps(const ArrayView& v, uint64_t* caps, cudaStream_t st);
 int launch_memory(const ArrayView& v, uint64_t* out2, cudaStream_t st);

@@ -428,10 +428,13 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(ArrayView v, const u
 //
 // The packed values are one contiguous stream in run order (round-major,
 // then block), and the runs of 32 consecutive (round, block) rows form one
-// contiguous span of it.  Each block takes a contiguous range of these
-// 32-row units.  Its producer warp resolves a unit lane-parallel (lane j =
-// row j: the run's first-value index, its LFVector, its position there and
-// the bucket address) and then cuts the unit's span into 16 KB windows: for
+// contiguous span of it.  Each block takes an equal, 16-byte aligned range
+// of the stream's bytes (so a few huge runs spread over every block as well
+// as many small ones do); a warp-wide 32-way search over the units' first
+// values finds the unit its range starts in.  Its producer warp resolves a
+// unit lane-parallel (lane j = row j: the run's first-value index, its
+// LFVector, its position there and the bucket address) and then cuts the
+// part of the unit's span inside the block's range into 16 KB windows: for
 // each, lane 0 fetches the window into a stage of a 3-deep shared-memory
 // ring with one TMA bulk copy (cp.async.bulk, mbarrier completion) and the
 // lanes write one descriptor per run piece in the window.  Two consumer
@@ -488,9 +491,15 @@ __global__ void __launch_bounds__(kBkThreads) copy_bulk_kernel(ArrayView v, cons
   // the spans would not describe the buffer, so nothing is read.
   if (sc.tile_pre[n_tiles] != n_values) return;
   const uint64_t n_units = (n_rows + kBkRows - 1) / kBkRows;
-  const uint64_t per = (n_units + gridDim.x - 1) / gridDim.x;
-  const uint64_t u0 = static_cast<uint64_t>(blockIdx.x) * per, u1 = min(n_units, u0 + per);
-  if (u0 >= u1) return;
+  // The block's bytes of the value stream.  Windows are 16-byte aligned and
+  // may reach up to 15 bytes past the last value: the stream starts 16-byte
+  // aligned and its end is not, in that case, so those bytes still lie in
+  // the same allocation (allocations end on a 256-byte boundary).
+  const uint64_t total = (n_values * E + 15) & ~static_cast<uint64_t>(15);
+  const uint64_t share = ((total + gridDim.x - 1) / gridDim.x + 15) & ~static_cast<uint64_t>(15);
+  const uint64_t blo = static_cast<uint64_t>(blockIdx.x) * share;
+  const uint64_t bhi = min(total, blo + share);
+  if (n_units == 0 || blo >= bhi) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kBkStages; ++s) {
@@ -505,7 +514,19 @@ __global__ void __launch_bounds__(kBkThreads) copy_bulk_kernel(ArrayView v, cons
     // ------------------------------- producer -------------------------------
     uint32_t i = 0;          // stages published so far
     bool ok = true;
-    for (uint64_t u = u0; u < u1 && ok; ++u) {
+    // The last unit whose first value starts at or before blo (32-way search;
+    // unit 0 starts at 0).
+    uint64_t ulo = 0, uhi = n_units;
+    while (uhi - ulo > 1) {
+      const uint64_t step = (uhi - ulo + 31) / 32;
+      const uint64_t pu = ulo + static_cast<uint64_t>(lane) * step;
+      const bool le = pu < uhi && voff_at(sc, pu * kBkRows, rows_per_tile, n_rows, n_tiles) * E <= blo;
+      const uint32_t m = __ballot_sync(0xffffffffu, le);
+      const uint64_t k = static_cast<uint64_t>(31 - __clz(static_cast<int>(m | 1u)));
+      ulo += k * step;
+      uhi = min(uhi, ulo + step);
+    }
+    for (uint64_t u = ulo; u < n_units && ok; ++u) {
       const uint64_t row = u * kBkRows + lane;
       const bool valid = row < n_rows;
       // Round trip 1: first-value index of this row's run and of the next.
@@ -533,9 +554,10 @@ __global__ void __launch_bounds__(kBkThreads) copy_bulk_kernel(ArrayView v, cons
       // The unit's span of values, cut into 16-byte aligned windows.
       const uint64_t span_lo = __shfl_sync(0xffffffffu, vs, 0) * E;
       const uint64_t span_hi = __shfl_sync(0xffffffffu, ve, 31) * E;
+      if (span_lo >= bhi) break;                 // this and every later unit lie past the block's range
       if (span_hi <= span_lo) continue;
-      const uint64_t w_first = span_lo & ~static_cast<uint64_t>(15);
-      const uint64_t w_end = (span_hi + 15) & ~static_cast<uint64_t>(15);
+      const uint64_t w_first = max(span_lo & ~static_cast<uint64_t>(15), blo);
+      const uint64_t w_end = min((span_hi + 15) & ~static_cast<uint64_t>(15), bhi);
       for (uint64_t wlo = w_first; wlo < w_end && ok; wlo += kBkWin, ++i) {
         const uint64_t whi = min(w_end, wlo + kBkWin);
         const int s = static_cast<int>(i % kBkStages);
@@ -706,6 +728,31 @@ int launch_insert(const ArrayView& v, const InsertScratch& s, const uint32_t* co
   else if (v.E == 8) GGA_COPY(8);
   else GGA_COPY(16);
 #undef GGA_COPY
+  return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Resize: the grow step of the growable-array experiment (Sec. VI-C, Table
+// II: the capacity is raised when necessary, before the insertion).  Every
+// LFVector l gets the buckets that make its capacity at least target[l]
+// (Algorithm 2 for each missing bucket, from the pool); sizes do not change.
+// One thread per LFVector; the pool's pops are folded by finalize_kernel.
+
+__global__ void __launch_bounds__(256) reserve_capacity_kernel(ArrayView v, const uint64_t* __restrict__ target) {
+  const uint32_t l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= v.L) return;
+  const uint32_t nb = v.nbuckets[l];
+  const uint32_t need = buckets_for(target[l], v.log2B);
+  if (need > nb) {
+    const uint32_t got = grow_buckets(v, l, nb, need);
+    v.nbuckets[l] = got;
+    if (got < need) latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
+  }
+}
+
+int launch_reserve(const ArrayView& v, const uint64_t* target, cudaStream_t st) {
+  reserve_capacity_kernel<<<(v.L + 255) / 256, 256, 0, st>>>(v, target);
+  finalize_kernel<<<1, 1024, 0, st>>>(v);
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }
 

@@ -33,7 +33,7 @@ DIST = {"bernoulli": 0, "uniform3": 1, "geometric": 2, "poisson": 3}
 MAX_THRESHOLDS = 16
 
 # Every symbol include/gga.h declares.
-EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
+EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
@@ -92,6 +92,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_insert": [vp, vp, u32, vp, u64, vp],
         "gga_insert_noalloc": [vp, vp, u32, vp, u64, vp],
         "gga_insert_generated": [vp, ctypes.POINTER(gga_gen_spec), u32, vp],
+        "gga_reserve": [vp, vp, vp],
         "gga_read": [vp, vp, u64, vp, vp],
         "gga_write": [vp, vp, u64, vp, vp],
         "gga_sweep": [vp, i32, u64, u32, vp],
@@ -233,6 +234,11 @@ def make_gen_spec(seed: int, dist: str, coeffs, round0: int = 0, thresholds=None
     s.va, s.vb, s.vc = va, vb, vc
     s.round0 = round0
     return s
+
+
+def gga_reserve(h, target: torch.Tensor, stream=None):
+    """target: device int64 tensor of L capacities (elements)."""
+    _check(load_library().gga_reserve(h, _dptr(target), _stream(stream)), "gga_reserve")
 
 
 def gga_insert_generated(h, spec: gga_gen_spec, rounds: int, stream=None):
@@ -405,6 +411,10 @@ class GGArray:
 
     def insert(self, counts, values, stream=None):
         gga_insert(self.h, counts, values, stream)
+
+    def reserve(self, target, stream=None):
+        """Capacity of LFVector l at least target[l] (device int64, L entries)."""
+        gga_reserve(self.h, target, stream)
 
     def insert_generated(self, spec, rounds, stream=None):
         gga_insert_generated(self.h, spec, rounds, stream)

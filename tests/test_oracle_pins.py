@@ -447,3 +447,47 @@ def test_served_random_read_matches_uniform_indices():
     got = a.read_random(4096, 99)
     idx = wl.uniform_indices(99, 4096, a.size())
     assert np.array_equal(got, flat[idx.astype(np.int64)])
+
+
+def _cap_closed_form(x: int, B: int) -> int:
+    # least B(2^k - 1) >= x, by logarithm rather than by walking the buckets
+    if x == 0:
+        return 0
+    k = int(np.ceil(np.log2(x / B + 1)))
+    while B * ((1 << k) - 1) < x:       # guard the float rounding at the edges
+        k += 1
+    while k > 0 and B * ((1 << (k - 1)) - 1) >= x:
+        k -= 1
+    return B * ((1 << k) - 1)
+
+
+@pytest.mark.parametrize("B", [1, 4, 256])
+def test_reserve_capacity_and_contents(B):
+    rng = np.random.default_rng(41 + B)
+    L, T, E = 6, 8, 4
+    o = oracle.OracleGGArray(L, T, B, E)
+    counts = rng.integers(0, 3, size=(3, L, T)).astype(np.uint32)
+    vals = (np.arange(int(counts.sum()), dtype=np.uint32) * 7 + 1)
+    o.insert(counts, vals)
+    sizes = o.sizes().astype(np.int64)
+    before = o.flatten().copy()
+    target = rng.integers(0, 5000, size=L).astype(np.uint64)
+    target[0] = 0
+    assert o.reserve(target) == oracle.OK
+    caps, nb = o.capacities()
+    for l in range(L):
+        want = _cap_closed_form(max(int(sizes[l]), int(target[l])), B)
+        assert int(caps[l]) == want
+        assert int(caps[l]) >= int(target[l])
+        assert int(caps[l]) == B * ((1 << int(nb[l])) - 1)
+    assert o.flatten().tobytes() == before.tobytes()           # a resize moves nothing
+    assert np.array_equal(o.sizes().astype(np.int64), sizes)
+    assert o.bucket_bytes() == int(caps.sum()) * E
+    # A smaller request changes nothing; an insertion past the reservation grows as usual.
+    assert o.reserve(target // np.uint64(2)) == oracle.OK
+    assert np.array_equal(o.capacities()[0], caps)
+    big = np.zeros((1, L, T), dtype=np.uint32)
+    big[0, 1, :] = 3000
+    o.insert(big, np.zeros(int(big.sum()), dtype=np.uint32))
+    caps2, _ = o.capacities()
+    assert int(caps2[1]) == _cap_closed_form(max(int(sizes[1]) + 3000 * T, int(target[1])), B)
