@@ -829,9 +829,10 @@ def run_doubling(args, world, rank, local):
     (gga_insert of one round: each LFVector's share split over its 1024
     threads, values packed in prefix-sum order), and a read/write pass adding
     +1 thirty times to every element (rw_b, the paper's per-block r/w).
-    GGArray with 32 and 512 LFVectors (first bucket 4096) and a static array
+    GGArray with 32 and 512 LFVectors (first bucket 4096), a static array
     allocated for the last size up front (no grow; contiguous copy for the
-    insertion, +30 in one pass with PyTorch)."""
+    insertion, +30 in one pass with PyTorch) and the memMap array (a reserved
+    address range grown by mapping more physical memory, no copy)."""
     import numpy as np
     from paper_2209_00103_gb300 import gga
     dev = torch.device("cuda", local)
@@ -907,6 +908,36 @@ def run_doubling(args, world, rank, local):
                          "rw_ms": round(e[1].elapsed_time(e[2]), 4)})
     rows["static"] = {"last": per_iter[-1], "iterations": per_iter, "mem_over_needed": 1.0}
     del a
+
+    # memMap: a reserved address range grown by mapping physical memory (no copy);
+    # grow is the host's mapping calls (wall clock), then the same insert and r/w.
+    vm = gga.GGAVMM(final * E)
+    size = n0
+    vm.grow(size * E)
+    vm.tensor(size)[:].copy_(values[:n0])
+    per_iter = []
+    for it in range(iters):
+        torch.cuda.synchronize(dev)
+        t_g = time.perf_counter()
+        vm.grow(2 * size * E)
+        grow_ms = (time.perf_counter() - t_g) * 1e3
+        view = vm.tensor(2 * size)
+        e = [ev() for _ in range(3)]
+        e[0].record(stream)
+        view[size:2 * size].copy_(values[:size])
+        e[1].record(stream)
+        view.add_(30)
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        size *= 2
+        per_iter.append({"size_after": size, "grow_ms": round(grow_ms, 4), "insert_ms": round(e[0].elapsed_time(e[1]), 4),
+                         "rw_ms": round(e[1].elapsed_time(e[2]), 4)})
+        del view
+    rows["memMap"] = {"last": per_iter[-1], "iterations": per_iter,
+                      "mem_over_needed": round(vm.info()["mapped_bytes"] / (final * E), 4),
+                      "grow": "host calls mapping the new physical memory (wall clock)"}
+    torch.cuda.synchronize(dev)
+    vm.close()
 
     last512 = rows["GGArray512"]["last"]
     peak, _ = peaks()

@@ -37,7 +37,8 @@ EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gg
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
-            "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy", "gga_append_batch", "gga_read_batch"]
+            "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy", "gga_append_batch", "gga_read_batch",
+            "gga_vmm_create", "gga_vmm_grow", "gga_vmm_info", "gga_vmm_destroy"]
 
 
 class gga_params(ctypes.Structure):
@@ -117,6 +118,10 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_append_batch": [ctypes.POINTER(gga_append_req), u32, vp],
         "gga_read_batch": [ctypes.POINTER(gga_read_req), u32, vp],
         "gga_twophase_work": [vp, u64, u32, vp],
+        "gga_vmm_create": [u64, ctypes.POINTER(vp)],
+        "gga_vmm_grow": [vp, u64],
+        "gga_vmm_info": [vp, ctypes.POINTER(u64)],
+        "gga_vmm_destroy": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -326,6 +331,41 @@ def gga_read_batch(reqs, stream=None):
         arr[i].array, arr[i].n, arr[i].seed = g.h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF
         arr[i].out = out.data_ptr()
     _check(load_library().gga_read_batch(arr, len(reqs), _stream(stream)), "gga_read_batch")
+
+
+class GGAVMM:
+    """The memMap comparison array (include/gga_vmm.h): a reserved range of
+    device addresses grown by mapping physical memory behind it, no copy.
+    tensor(n, dtype) is a zero-copy view of the first n elements."""
+
+    def __init__(self, max_bytes: int):
+        self.h = ctypes.c_void_p()
+        _check(load_library().gga_vmm_create(int(max_bytes), ctypes.byref(self.h)), "gga_vmm_create")
+
+    def grow(self, nbytes: int):
+        _check(load_library().gga_vmm_grow(self.h, int(nbytes)), "gga_vmm_grow")
+
+    def info(self):
+        out = (ctypes.c_uint64 * 3)()
+        _check(load_library().gga_vmm_info(self.h, out), "gga_vmm_info")
+        return {"address": int(out[0]), "mapped_bytes": int(out[1]), "granularity": int(out[2])}
+
+    def tensor(self, n: int, dtype=torch.int32) -> torch.Tensor:
+        inf = self.info()
+        itemsize = torch.empty(0, dtype=dtype).element_size()
+        if n * itemsize > inf["mapped_bytes"]:
+            raise ValueError("view beyond the mapped part")
+        typestr = {torch.int32: "<i4", torch.int64: "<i8", torch.uint8: "|u1"}[dtype]
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (inf["address"], False),
+                                        "version": 2, "strides": None}
+        return torch.as_tensor(_View(), device="cuda")
+
+    def close(self):
+        if self.h:
+            _check(load_library().gga_vmm_destroy(self.h), "gga_vmm_destroy")
+            self.h = ctypes.c_void_p()
 
 
 class GGABatch:
