@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--no-baselines", action="store_true", help="skip the static / semi-static flat arrays")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling"],
+    ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling",
+                                           "insertion"],
                     default="paper_growth",
                     help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch; "
                          "served: continuous-batching request server")
@@ -961,6 +962,55 @@ def run_doubling(args, world, rank, local):
                                        "GGArray32": {"grow": 0.52, "insert": 27.90, "rw": 198.32}}}
 
 
+def run_insertion(args, world, rank, local):
+    """The insertion experiment of the paper's Sec. VI-A: a static (flat)
+    array of 10^6 int32 elements with room to double 10 times; each doubling
+    inserts one element per element already there, with one thread per new
+    element, by Sec. III-B's atomic approach (one atomicAdd per thread) and by
+    its warp-shuffle scan approach (one atomicAdd per block), for several
+    block sizes.  (The tensor-core scan is not built.)"""
+    from paper_2209_00103_gb300 import gga
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n0, iters = 1_000_000, 10
+    final = n0 << iters
+    a = torch.empty(final, dtype=torch.int32, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    rows = {}
+    for mode, name in ((gga.GGA_FLAT_SCAN, "scan"), (gga.GGA_FLAT_ATOMIC, "atomic")):
+        for T in (128, 256, 512, 1024):
+            size.fill_(n0)
+            s_host = n0
+            per_iter = []
+            for it in range(iters):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gga.gga_flat_insert(mode, a, size, s_host, T, s_host, stream)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                s_host *= 2
+                per_iter.append(round(e0.elapsed_time(e1), 4))
+            if int(size.item()) != final:
+                raise RuntimeError(f"insertion {name} T={T}: size {int(size.item())} vs {final}")
+            rows[f"{name}_T{T}"] = {"iterations_ms": per_iter, "last_ms": per_iter[-1],
+                                    "last_gelem_s": round((final // 2) / (per_iter[-1] / 1e3) / 1e9, 2)}
+    best_scan = min((v["last_ms"], k) for k, v in rows.items() if k.startswith("scan"))
+    best_atomic = min((v["last_ms"], k) for k, v in rows.items() if k.startswith("atomic"))
+    peak, _ = peaks()
+    gbs = (final // 2) * 4 / (best_scan[0] / 1e3) / 1e9
+    return {"metric": "insertion approaches on a flat array (Sec. VI-A): last doubling 5.12e8 -> 1.024e9 int32",
+            "value": round((final // 2) / (best_scan[0] / 1e3) / 1e9, 3), "unit": "Gelem/s (best scan)",
+            "n_gpus": world, "steps": iters, "warmup": 0, "ms_per_step": best_scan[0], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "flat_insertion_doubling_1e6_x2_10_int32", "start": n0, "final": final},
+            "roofline": {"bound": "hbm", "kernel": f"flat_insert_scan_kernel ({best_scan[1]})", "achieved": round(gbs, 1),
+                         "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 3), "traffic": None},
+            "best": {"scan": best_scan[1], "atomic": best_atomic[1],
+                     "atomic_over_scan": round(best_atomic[0] / best_scan[0], 2)},
+            "table": rows}
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -974,6 +1024,8 @@ def main():
         res = run_two_phase(args, world, rank, local)
     elif args.workload == "doubling":
         res = run_doubling(args, world, rank, local)
+    elif args.workload == "insertion":
+        res = run_insertion(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -38,7 +38,7 @@ EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gg
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
             "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy", "gga_append_batch", "gga_read_batch",
-            "gga_vmm_create", "gga_vmm_grow", "gga_vmm_info", "gga_vmm_destroy"]
+            "gga_vmm_create", "gga_vmm_grow", "gga_vmm_info", "gga_vmm_destroy", "gga_flat_insert"]
 
 
 class gga_params(ctypes.Structure):
@@ -118,6 +118,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_append_batch": [ctypes.POINTER(gga_append_req), u32, vp],
         "gga_read_batch": [ctypes.POINTER(gga_read_req), u32, vp],
         "gga_twophase_work": [vp, u64, u32, vp],
+        "gga_flat_insert": [i32, vp, u64, vp, u64, u32, u32, vp],
         "gga_vmm_create": [u64, ctypes.POINTER(vp)],
         "gga_vmm_grow": [vp, u64],
         "gga_vmm_info": [vp, ctypes.POINTER(u64)],
@@ -331,6 +332,21 @@ def gga_read_batch(reqs, stream=None):
         arr[i].array, arr[i].n, arr[i].seed = g.h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF
         arr[i].out = out.data_ptr()
     _check(load_library().gga_read_batch(arr, len(reqs), _stream(stream)), "gga_read_batch")
+
+
+GGA_FLAT_ATOMIC = 0
+GGA_FLAT_SCAN = 1
+
+
+def gga_flat_insert(mode: int, array: torch.Tensor, size: torch.Tensor, n_threads: int, threads_per_block: int,
+                    first_value: int = 0, stream=None):
+    """Sec. III-B insertion approaches on a flat uint32 array (include/gga_flat.h).
+    array: device int32 tensor (capacity = its length); size: device int64
+    tensor of one element, advanced by n_threads."""
+    assert array.dtype == torch.int32 and size.dtype == torch.int64 and size.numel() == 1
+    _check(load_library().gga_flat_insert(int(mode), _dptr(array), array.numel(), _dptr(size), int(n_threads),
+                                          int(threads_per_block), int(first_value) & 0xFFFFFFFF, _stream(stream)),
+           "gga_flat_insert")
 
 
 class GGAVMM:
