@@ -57,7 +57,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling",
-                                           "insertion"],
+                                           "insertion", "phases"],
                     default="paper_growth",
                     help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch; "
                          "served: continuous-batching request server")
@@ -1011,6 +1011,124 @@ def run_insertion(args, world, rank, local):
             "table": rows}
 
 
+def run_phases(args, world, rank, local):
+    """The two-phase case study of the paper's Sec. VI-D, against memMap:
+    every iteration inserts k times the array's size (k = 1, 3, 10), then
+    runs a work phase of W kernels adding 1 to every element (W = 1 .. 1000);
+    four iterations, starting from 10^9 / (1+k)^4 so that the final size is
+    10^9 int32.  GGArray (512 LFVectors, 1024 threads, first bucket 4096):
+    insertion with gga_insert, then flatten into a contiguous array the work
+    runs on.  memMap: grow by mapping, the insertion copied into the mapped
+    range, the work on it directly.  Host wall time of all iterations,
+    synchronized before and after; speedup = memMap time / GGArray time."""
+    import numpy as np
+    from paper_2209_00103_gb300 import gga
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    L, T, B, E, iters = 512, 1024, 4096, 4, 4
+    Ws = (1, 10, 100, 1000)
+    final_target = 10 ** 9
+
+    def split(n, parts):
+        return np.array([n // parts + (1 if i < n % parts else 0) for i in range(parts)], dtype=np.int64)
+
+    # Warm-up: load every kernel both variants use (insert, flatten, the +1
+    # pass, the mapping calls) before anything is timed.
+    wg = gga.GGArray(L, T, B, E, 64 << 20)
+    wc = torch.ones((1, L, T), dtype=torch.int32, device=dev)
+    wv = torch.arange(L * T, dtype=torch.int32, device=dev)
+    wg.insert(wc, wv, stream)
+    wf = torch.empty(L * T, dtype=torch.int32, device=dev)
+    wg.flatten(wf, stream)
+    wf.add_(1)
+    wvm = gga.GGAVMM(64 << 20)
+    wvm.grow(4 << 20)
+    wvm.tensor(1 << 20)[:].copy_(wv[:1 << 19].repeat(2))
+    wvm.tensor(1 << 20).add_(1)
+    torch.cuda.synchronize(dev)
+    wvm.close()
+    wg.close()
+    del wc, wv, wf
+
+    out = {}
+    for k in (1, 3, 10):
+        start = round(final_target / (1 + k) ** iters)
+        final = start * (1 + k) ** iters
+        max_add = final - final // (1 + k)
+        values = torch.arange(max_add, dtype=torch.int32, device=dev)
+        flat = torch.empty(final, dtype=torch.int32, device=dev)
+        rows = {}
+        for W in Ws:
+            # GGArray
+            g = gga.GGArray(L, T, B, E, int(2.3 * final * E) + L * B * E * 4)
+            sizes = split(start, L)
+            c0 = np.zeros((1, L, T), dtype=np.uint32)
+            for l in range(L):
+                c0[0, l, :] = split(int(sizes[l]), T)
+            g.insert(torch.from_numpy(c0.view(np.int32)).to(dev), values[:start], stream)
+            counts = []
+            sz = sizes.copy()
+            for it in range(iters):
+                c = np.zeros((1, L, T), dtype=np.uint32)
+                for l in range(L):
+                    c[0, l, :] = split(int(k * sz[l]), T)
+                counts.append(torch.from_numpy(c.view(np.int32)).to(dev))
+                sz = sz * (1 + k)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            n = start
+            t_ins = t_flat = 0.0
+            for it in range(iters):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                g.insert(counts[it], values[:k * n], stream)
+                e[1].record(stream)
+                n = n * (1 + k)
+                g.flatten(flat[:n], stream)
+                e[2].record(stream)
+                view = flat[:n]
+                for _ in range(W):
+                    view.add_(1)
+                torch.cuda.synchronize(dev)
+                t_ins += e[0].elapsed_time(e[1])
+                t_flat += e[1].elapsed_time(e[2])
+            gg_ms = (time.perf_counter() - t0) * 1e3
+            if g.size(stream)[0] != final:
+                raise RuntimeError("phases: GGArray size mismatch")
+            g.close()
+            # memMap
+            vm = gga.GGAVMM(final * E)
+            vm.grow(start * E)
+            vm.tensor(start)[:].copy_(values[:start])
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            n = start
+            for it in range(iters):
+                vm.grow((1 + k) * n * E)
+                view = vm.tensor((1 + k) * n)
+                view[n:].copy_(values[:k * n])
+                n = n * (1 + k)
+                for _ in range(W):
+                    view.add_(1)
+                del view
+            torch.cuda.synchronize(dev)
+            mm_ms = (time.perf_counter() - t0) * 1e3
+            vm.close()
+            rows[f"W{W}"] = {"ggarray_ms": round(gg_ms, 3), "ggarray_insert_ms": round(t_ins, 3),
+                             "ggarray_flatten_ms": round(t_flat, 3), "memmap_ms": round(mm_ms, 3),
+                             "speedup_ggarray_over_memmap": round(mm_ms / gg_ms, 3)}
+        out[f"k{k}"] = {"start": start, "final": final, "rows": rows}
+        del values, flat
+    w1 = out["k1"]["rows"]["W1"]
+    return {"metric": "two-phase case study (Sec. VI-D): speedup of GGArray over memMap",
+            "value": w1["speedup_ggarray_over_memmap"], "unit": "x (k=1, W=1)", "n_gpus": world,
+            "steps": iters, "warmup": 0, "ms_per_step": w1["ggarray_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "two_phase_vs_memmap_final1e9_int32", "L": L, "T": T, "B": B,
+                       "iterations": iters, "insert_factors": [1, 3, 10], "work_kernels": list(Ws)},
+            "table": out}
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -1026,6 +1144,8 @@ def main():
         res = run_doubling(args, world, rank, local)
     elif args.workload == "insertion":
         res = run_insertion(args, world, rank, local)
+    elif args.workload == "phases":
+        res = run_phases(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:
