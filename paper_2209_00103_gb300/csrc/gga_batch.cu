@@ -3,11 +3,12 @@
 // A batch is a list of jobs: an array, the draws of its counts and values
 // (as gga_insert_generated), and a target size.  gga_batch_grow runs one
 // persistent kernel over all (array, LFVector) items, largest first, taken
-// from an atomic ticket: a block grows its LFVector round by round -- every
-// thread draws its count, a block scan gives positions, counts are clipped
-// at the LFVector's target by the same scan, the leader reserves and
-// allocates, the block writes (Algorithm 1 with thread coarsening: a block
-// of 128 threads plays T <= 1024 threads).  Then one kernel folds the pool
+// from an atomic ticket: a block grows its LFVector in passes of several
+// rounds -- every thread draws its counts, a block scan gives positions,
+// counts are clipped at the LFVector's target by the same scan, the leader
+// reserves and allocates, the block stages the values and writes them with
+// 128-bit stores (Algorithm 1 with thread coarsening: a block of 512 threads
+// plays T <= 1024 threads).  Then one kernel folds the pool
 // pops and one finalizes every array.  Nothing allocates and nothing waits
 // on the host, so the whole step can be captured in a CUDA graph and
 // replayed (gga_batch_capture / gga_batch_replay).
@@ -23,8 +24,8 @@ int launch_clear(const ArrayView& v, cudaStream_t st);
 
 namespace {
 
-constexpr int kBatchThreads = 128;
-constexpr int kBatchMaxK = 8;              // virtual threads per physical thread (T <= 1024)
+constexpr int kBatchThreads = 512;        // up to 2 virtual threads per thread (T <= 1024)
+constexpr uint32_t kBatchStageBytes = 49152;
 constexpr uint32_t kBatchMaxRounds = 1u << 20;
 
 struct BatchJob {
@@ -38,112 +39,24 @@ struct BatchItem {
   uint32_t l;
 };
 
+// Grow LFVector l of job J to its share of the target: rounds of in-thread
+// insertions in passes of K (grow_passes in gga_gen.cuh), clipped at the
+// target.  All threads of the block call it.
 template <int E>
-__device__ __forceinline__ void put_elem(uint64_t addr, uint64_t val) {
-  typedef typename Elem<E>::T T;
-  *reinterpret_cast<T*>(addr) = gen_value<E>(val);
-}
-
-// Grow LFVector l of job J to its target.  All kBatchThreads threads call it.
-template <int E>
-__device__ void grow_item(const BatchJob& J, uint32_t l, uint32_t* s_wsum, uint64_t* s_state) {
+__device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* stage) {
   const ArrayView& v = J.v;
-  const GenParams& g = J.g;
-  const uint32_t t0 = threadIdx.x, lane = t0 & 31, warp = t0 >> 5;
-  const uint32_t k = (v.T + kBatchThreads - 1) / kBatchThreads;   // virtual threads per thread
   const uint64_t target = J.target / v.L + (l < J.target % v.L ? 1 : 0);
-  const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
-  if (t0 == 0) {
-    s_state[0] = v.sizes[l];      // size
-    s_state[1] = v.nbuckets[l];   // allocated buckets
-    s_state[2] = 0;               // stop flag
-  }
+  const uint32_t drawn = grow_passes<E, (E == 16 ? 4 : 8), 2>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
+                                                             kBatchStageBytes / E);
+  if (threadIdx.x == 0 && sh.stop == 0 && drawn >= kBatchMaxRounds) latch_error(v.status, GGA_ERR_TIMEOUT);
   __syncthreads();
-  uint32_t rounds = 0;
-  for (uint64_t r = g.round0;; ++r, ++rounds) {
-    const uint64_t size = s_state[0];
-    if (size >= target || s_state[2]) break;
-    if (rounds >= kBatchMaxRounds) {
-      if (t0 == 0) latch_error(v.status, GGA_ERR_TIMEOUT);
-      break;
-    }
-    // Draw this thread's k virtual counts (virtual thread t = t0 * k + i).
-    uint32_t c[kBatchMaxK];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int i = 0; i < kBatchMaxK; ++i) {
-      const uint32_t t = t0 * k + i;
-      c[i] = 0;
-      if (static_cast<uint32_t>(i) < k && t < v.T)
-        c[i] = gen_count(g, splitmix(g.seed, (r << 32) | (static_cast<uint64_t>(l) * v.T + t)));
-      sum += c[i];
-    }
-    // Block exclusive scan of the per-thread sums.
-    uint32_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t n = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= static_cast<uint32_t>(o)) inc += n;
-    }
-    if (lane == 31) s_wsum[warp] = inc;
-    __syncthreads();
-    uint32_t wpre = 0, total = 0;
-#pragma unroll
-    for (int w = 0; w < kBatchThreads / 32; ++w) {
-      const uint32_t x = s_wsum[w];
-      if (static_cast<uint32_t>(w) < warp) wpre += x;
-      total += x;
-    }
-    const uint64_t rem = target - size;
-    const uint64_t commit = total < rem ? total : rem;   // counts past the target are clipped
-    if (t0 == 0 && commit) {
-      // Leader: reservation and Algorithm 2 for the buckets it reaches.
-      const uint32_t nb = static_cast<uint32_t>(s_state[1]);
-      const uint32_t need = buckets_for(size + commit, v.log2B);
-      if (need > nb) {
-        const uint32_t got = grow_buckets(v, l, nb, need);
-        s_state[1] = got;
-        v.nbuckets[l] = got;
-        if (got < need) {
-          s_state[2] = 1;
-          latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
-        }
-      }
-    }
-    __syncthreads();   // synchronize(): buckets exist before any write
-    if (!s_state[2]) {
-      uint64_t run = wpre + inc - sum;   // this thread's first position in the round
-#pragma unroll
-      for (int i = 0; i < kBatchMaxK; ++i) {
-        const uint32_t t = t0 * k + i;
-        if (c[i] && run < commit) {
-          const uint64_t gtid = static_cast<uint64_t>(l) * v.T + t;
-          const uint64_t take = min(static_cast<uint64_t>(c[i]), commit - run);
-          uint64_t val = g.va * gtid + g.vb * r;
-          for (uint64_t m = 0; m < take; ++m, val += g.vc) {
-            uint32_t bb;
-            uint64_t off;
-            bucket_of(size + run + m, v.log2B, bb, off);
-            put_elem<E>(bk[bb] + off * E, val);
-          }
-        }
-        run += c[i];
-      }
-    }
-    __syncthreads();
-    if (t0 == 0 && !s_state[2]) {
-      s_state[0] = size + commit;
-      v.sizes[l] = size + commit;
-    }
-    __syncthreads();
-  }
 }
 
-__global__ void __launch_bounds__(kBatchThreads) batch_grow_kernel(const BatchJob* __restrict__ jobs,
-                                                                   const BatchItem* __restrict__ items,
-                                                                   uint32_t n_items, uint32_t* ticket) {
-  __shared__ uint32_t s_wsum[kBatchThreads / 32];
-  __shared__ uint64_t s_state[3];
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_grow_kernel(const BatchJob* __restrict__ jobs,
+                                                                      const BatchItem* __restrict__ items,
+                                                                      uint32_t n_items, uint32_t* ticket) {
+  extern __shared__ uint4 s_stage4[];
+  __shared__ GenShared sh;
   __shared__ uint32_t s_item;
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
@@ -154,9 +67,9 @@ __global__ void __launch_bounds__(kBatchThreads) batch_grow_kernel(const BatchJo
     const BatchItem item = items[it];
     const BatchJob& J = jobs[item.job];
     switch (J.v.E) {
-      case 4: grow_item<4>(J, item.l, s_wsum, s_state); break;
-      case 8: grow_item<8>(J, item.l, s_wsum, s_state); break;
-      default: grow_item<16>(J, item.l, s_wsum, s_state); break;
+      case 4: grow_item<4>(J, item.l, sh, s_stage4); break;
+      case 8: grow_item<8>(J, item.l, sh, s_stage4); break;
+      default: grow_item<16>(J, item.l, sh, s_stage4); break;
     }
   }
 }
@@ -212,7 +125,8 @@ namespace {
 
 int batch_grow(gga_batch_t* b, cudaStream_t st) {
   if (b->n_items) {
-    gga::batch_grow_kernel<<<b->grid, gga::kBatchThreads, 0, st>>>(b->jobs, b->items, b->n_items, b->ticket);
+    gga::batch_grow_kernel<<<b->grid, gga::kBatchThreads, gga::kBatchStageBytes, st>>>(b->jobs, b->items,
+                                                                                         b->n_items, b->ticket);
     gga::batch_fixup_kernel<<<(b->n_pools + 63) / 64 + 1, 64, 0, st>>>(b->pools, b->n_pools, b->ticket);
   }
   if (b->n_jobs) gga::batch_finalize_kernel<<<b->n_jobs, 256, 0, st>>>(b->jobs);
@@ -275,8 +189,10 @@ int gga_batch_create(const gga_batch_job* jobs, uint32_t n_jobs, void* stream, g
   }
   b->num_sms = num_sms;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gga::batch_grow_kernel, gga::kBatchThreads, 0) !=
-          cudaSuccess ||
+  cudaFuncSetAttribute(gga::batch_grow_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(gga::kBatchStageBytes));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gga::batch_grow_kernel, gga::kBatchThreads,
+                                                    gga::kBatchStageBytes) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   b->grid = static_cast<unsigned>(num_sms * per_sm);

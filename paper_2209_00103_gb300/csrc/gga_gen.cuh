@@ -127,4 +127,201 @@ __device__ inline void finalize_block(const ArrayView& v, const uint64_t* ins_ba
 }
 
 
+// ---------------------------------------------------------------------------
+// Growth of one LFVector by rounds of in-thread insertions (the in-kernel
+// push_back of Algorithm 1, positions from Sec. III-B's block prefix sum),
+// K rounds per pass.  Shared by the generated insertion (one block per
+// LFVector, a fixed number of rounds) and the batched growth (a persistent
+// block per item, rounds until the LFVector's target).
+//
+// Per pass every thread draws its counts for K rounds (virtual threads
+// t = t0 * kv + i, kv = ceil(T / blockDim) <= KV), the per-thread round sums
+// are scanned two rounds per 32-bit word (sums < 2^16 per block: counts are
+// below 64 and blockDim * kv <= 1024), thread 0 makes one size reservation
+// for the pass -- clipped at `target`, and, if the pool cannot hold the
+// buckets it reaches, cut back to the longest prefix of whole rounds that
+// fits -- and takes the buckets (Algorithm 2); then (synchronize) the values
+// go to a shared-memory stage at their positions and the block streams the
+// stage to the buckets with aligned 128-bit stores (a pass larger than the
+// stage writes straight to the buckets).  Elements past the target are the
+// ones a round-by-round growth would clip (positions are round-major).
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+struct GenShared {
+  uint32_t wt[4][32];   // packed warp prefixes (K / 2 <= 4 words)
+  uint32_t rb[9];       // pass-relative start of every round (K <= 8)
+  uint64_t base;        // LFVector size before the pass
+  uint32_t commit, nb;
+  int stop;             // 1: pool exhausted, 2: target reached
+};
+
+template <int E>
+__device__ __forceinline__ void put_gen_elem(uint64_t addr, typename Elem<E>::T x) {
+  *reinterpret_cast<typename Elem<E>::T*>(addr) = x;
+}
+
+// Returns the number of rounds it drew.  Every thread of the block calls it.
+template <int E, int K, int KV>
+__device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t l, uint32_t R, uint64_t target,
+                                GenShared& sh, uint4* stage4, uint32_t cap) {
+  typedef typename Elem<E>::T T;
+  constexpr uint32_t VEC = 16 / E;
+  constexpr int KP = K / 2;
+  static_assert(K % 2 == 0 && K <= 8, "K rounds per pass: even, at most 8");
+  T* stage = reinterpret_cast<T*>(stage4);
+  const uint32_t t0 = threadIdx.x, NT = blockDim.x;
+  const int lane = t0 & 31, warp = t0 >> 5, nwarps = NT >> 5;
+  const uint32_t kv = KV == 1 ? 1u : (v.T + NT - 1) / NT;
+  const uint64_t tfirst = static_cast<uint64_t>(t0) * kv;        // first virtual thread
+  const uint64_t gfirst = static_cast<uint64_t>(l) * v.T + tfirst;
+  const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
+  const bool group_ok = v.B >= VEC;
+  if (t0 == 0) {
+    sh.base = v.sizes[l];
+    sh.nb = v.nbuckets[l];
+    sh.stop = sh.base >= target ? 2 : 0;
+  }
+  __syncthreads();
+  uint32_t r0 = 0;
+  while (r0 < R && sh.stop == 0) {
+    const uint32_t kk = min(static_cast<uint32_t>(K), R - r0);
+    uint32_t pk[KP], inc[KP], cc[K];
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      uint32_t c[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = 2 * j + h;
+        const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
+        uint32_t c0 = 0, c1 = 0;
+        if (k < kk) {
+          if (tfirst < v.T) c0 = gen_count(g, splitmix(g.seed, (r << 32) | gfirst));
+          if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = gen_count(g, splitmix(g.seed, (r << 32) | (gfirst + 1)));
+        }
+        cc[k] = c0 | (c1 << 8);
+        c[h] = c0 + c1;
+      }
+      pk[j] = c[0] | (c[1] << 16);
+      inc[j] = warp_incl_scan_u32(pk[j]);
+      if (lane == 31) sh.wt[j][warp] = inc[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t rb = 0;
+#pragma unroll
+      for (int j = 0; j < KP; ++j) {
+        const uint32_t w = lane < nwarps ? sh.wt[j][lane] : 0u;
+        const uint32_t wi = warp_incl_scan_u32(w);
+        if (lane < nwarps) sh.wt[j][lane] = wi - w;
+        const uint32_t tot = __shfl_sync(0xffffffffu, wi, 31);
+        if (lane == 0) {
+          sh.rb[2 * j] = rb;
+          rb += tot & 0xFFFFu;
+          sh.rb[2 * j + 1] = rb;
+          rb += tot >> 16;
+        }
+      }
+      if (lane == 0) {
+        sh.rb[K] = rb;
+        const uint64_t base = sh.base;
+        const uint64_t rem = target - base;   // > 0 while the loop runs
+        uint32_t commit = rb < rem ? rb : static_cast<uint32_t>(rem);
+        if (commit > 0) {
+          const uint32_t nb = sh.nb;
+          const uint32_t need = buckets_for(base + commit, v.log2B);
+          if (need > nb) {
+            const uint32_t got = grow_buckets(v, l, nb, need);
+            sh.nb = got;
+            v.nbuckets[l] = got;
+            if (got < need) {
+              const uint64_t capg = bucket_first(got, v.log2B);
+              int kf = 0;
+              while (kf < K && base + sh.rb[kf + 1] <= capg) ++kf;
+              if (sh.rb[kf] < commit) commit = sh.rb[kf];
+              sh.stop = 1;
+              latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
+            }
+          }
+        }
+        if (sh.stop == 0 && base + commit >= target) sh.stop = 2;
+        sh.commit = commit;
+        v.sizes[l] = base + commit;
+      }
+    }
+    __syncthreads();   // synchronize(): the buckets exist before any write
+
+    const uint64_t base = sh.base;
+    const uint32_t commit = sh.commit;
+    const uint32_t shv = static_cast<uint32_t>(base & (VEC - 1));   // stage index = pass position + shv
+    const bool staged = commit + shv <= cap;
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+      const uint32_t ex = sh.wt[j][warp] + inc[j] - pk[j];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t k = 2 * j + h;
+        uint32_t st = sh.rb[k] + ((ex >> (16 * h)) & 0xFFFFu);
+#pragma unroll
+        for (int i = 0; i < KV; ++i) {
+          const uint32_t c = (cc[k] >> (8 * i)) & 0xFFu;
+          if (c == 0) continue;
+          uint64_t val = g.va * (gfirst + i) + g.vb * (static_cast<uint64_t>(g.round0) + r0 + k);
+          for (uint32_t m = 0; m < c; ++m, val += g.vc) {
+            const uint32_t q = st + m;
+            if (q >= commit) break;
+            if (staged) {
+              stage[q + shv] = gen_value<E>(val);
+            } else {
+              uint32_t bb;
+              uint64_t off;
+              bucket_of(base + q, v.log2B, bb, off);
+              put_gen_elem<E>(bk[bb] + off * E, gen_value<E>(val));
+            }
+          }
+          st += c;
+        }
+      }
+    }
+    __syncthreads();
+    if (staged && commit) {
+      const uint64_t gbeg = base - shv;
+      const uint32_t nvec = (commit + shv + VEC - 1) / VEC;
+      for (uint32_t vi = t0; vi < nvec; vi += NT) {
+        const uint64_t p = gbeg + static_cast<uint64_t>(vi) * VEC;
+        const uint32_t lo = vi * VEC;   // stage index of p
+        if (group_ok && lo >= shv && lo + VEC <= commit + shv) {
+          uint32_t bb;
+          uint64_t off;
+          bucket_of(p, v.log2B, bb, off);
+          __stcs(reinterpret_cast<uint4*>(bk[bb] + off * E), stage4[vi]);
+        } else {
+#pragma unroll
+          for (uint32_t e = 0; e < VEC; ++e) {
+            const uint32_t si = lo + e;
+            if (si < shv || si >= commit + shv) continue;
+            uint32_t bb;
+            uint64_t off;
+            bucket_of(p + e, v.log2B, bb, off);
+            put_gen_elem<E>(bk[bb] + off * E, stage[si]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (t0 == 0) sh.base = base + commit;
+    r0 += kk;
+    __syncthreads();
+  }
+  return r0;
+}
+
 }  // namespace gga

@@ -775,175 +775,13 @@ constexpr int kGenMinBlocks512 = 3;
 
 template <int E> struct GenK { static constexpr int value = E == 16 ? 4 : 8; };
 
-// Warp inclusive scan of two 16-bit counters packed in one word.  Counts per
-// thread are below 64, so a warp sums below 2^11 and a block of <= 1024
-// threads below 2^16: no carry crosses the halves.
-__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += n;
-  }
-  return v;
-}
-
-// One block per LFVector.  Per pass of K rounds: every thread draws its K
-// counts (two rounds per 32-bit word), a warp-shuffle scan plus one
-// shared-memory pass over the warp totals gives every (round, thread) its
-// position (Sec. III-B), thread 0 reserves the pass's run with one size
-// update and allocates the buckets it reaches (Algorithms 1-2), then
-// (synchronize) every thread writes its values at its positions into a
-// shared-memory stage, and the block streams the stage to the buckets with
-// aligned 128-bit stores.  A pass that does not fit the stage writes straight
-// to the buckets instead.
+// One block per LFVector, R rounds in passes of K (grow_passes in
+// gga_gen.cuh), with no target.
 template <int E, int K, int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) gen_insert_kernel(ArrayView v, GenParams g, uint32_t R) {
-  typedef typename Elem<E>::T T;
-  constexpr uint32_t VEC = 16 / E;
-  constexpr uint32_t CAP = kGenStageBytes / E;
-  constexpr int KP = K / 2;   // packed words per thread
   extern __shared__ uint4 s_stage4[];
-  T* s_stage = reinterpret_cast<T*>(s_stage4);
-  __shared__ uint32_t s_wt[KP][32];      // packed warp prefixes
-  __shared__ uint32_t s_rb[K + 1];       // pass-relative start of every round
-  __shared__ uint64_t s_base;
-  __shared__ uint32_t s_commit, s_nb;
-  __shared__ int s_stop;
-
-  const uint32_t l = blockIdx.x, t = threadIdx.x, NT = blockDim.x;
-  const int lane = t & 31, warp = t >> 5, nwarps = NT >> 5;
-  const uint64_t gtid = static_cast<uint64_t>(l) * v.T + t;
-  const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
-  const bool group_ok = v.B >= VEC;
-  const bool active = t < v.T;
-  if (t == 0) {
-    s_base = v.sizes[l];
-    s_nb = v.nbuckets[l];
-    s_stop = 0;
-  }
-  __syncthreads();
-
-  for (uint32_t r0 = 0; r0 < R; r0 += K) {
-    const uint32_t kk = min(static_cast<uint32_t>(K), R - r0);
-    uint32_t pk[KP], inc[KP];
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      uint32_t c[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t k = 2 * j + h;
-        const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
-        c[h] = (active && k < kk) ? gen_count(g, splitmix(g.seed, (r << 32) | gtid)) : 0u;
-      }
-      pk[j] = c[0] | (c[1] << 16);
-      inc[j] = warp_incl_scan_u32(pk[j]);
-      if (lane == 31) s_wt[j][warp] = inc[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t rb = 0;
-#pragma unroll
-      for (int j = 0; j < KP; ++j) {
-        const uint32_t w = lane < nwarps ? s_wt[j][lane] : 0u;
-        const uint32_t wi = warp_incl_scan_u32(w);
-        if (lane < nwarps) s_wt[j][lane] = wi - w;
-        const uint32_t tot = __shfl_sync(0xffffffffu, wi, 31);
-        if (lane == 0) {
-          s_rb[2 * j] = rb;
-          rb += tot & 0xFFFFu;
-          s_rb[2 * j + 1] = rb;
-          rb += tot >> 16;
-        }
-      }
-      if (lane == 0) {
-        s_rb[K] = rb;
-        // Leader: one size reservation for the pass, then Algorithm 2 for
-        // every bucket the run reaches.
-        const uint64_t base = s_base;
-        uint32_t commit = rb;
-        if (rb > 0) {
-          const uint32_t nb = s_nb;
-          const uint32_t need = buckets_for(base + rb, v.log2B);
-          if (need > nb) {
-            const uint32_t got = grow_buckets(v, l, nb, need);
-            s_nb = got;
-            v.nbuckets[l] = got;
-            if (got < need) {
-              const uint64_t cap = bucket_first(got, v.log2B);
-              int kf = 0;
-              while (kf < K && base + s_rb[kf + 1] <= cap) ++kf;
-              commit = s_rb[kf];
-              s_stop = 1;
-              latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
-            }
-          }
-        }
-        s_commit = commit;
-        v.sizes[l] = base + commit;
-      }
-    }
-    __syncthreads();   // synchronize(): the buckets exist before any write
-
-    const uint64_t base = s_base;
-    const uint32_t commit = s_commit;
-    const uint32_t sh = static_cast<uint32_t>(base & (VEC - 1));   // stage index = pass position + sh
-    const bool staged = commit + sh <= CAP;
-#pragma unroll
-    for (int j = 0; j < KP; ++j) {
-      const uint32_t ex = s_wt[j][warp] + inc[j] - pk[j];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const uint32_t k = 2 * j + h;
-        const uint32_t c = (pk[j] >> (16 * h)) & 0xFFFFu;
-        if (c == 0) continue;
-        const uint32_t st = s_rb[k] + ((ex >> (16 * h)) & 0xFFFFu);
-        uint64_t val = g.va * gtid + g.vb * (static_cast<uint64_t>(g.round0) + r0 + k);
-        for (uint32_t m = 0; m < c; ++m, val += g.vc) {
-          const uint32_t q = st + m;
-          if (q >= commit) break;
-          if (staged) {
-            s_stage[q + sh] = gen_value<E>(val);
-          } else {
-            uint32_t bb;
-            uint64_t off;
-            bucket_of(base + q, v.log2B, bb, off);
-            store_elem<E>(bk[bb] + off * E, gen_value<E>(val));
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (staged && commit) {
-      const uint64_t gbeg = base - sh;
-      const uint32_t nvec = (commit + sh + VEC - 1) / VEC;
-      for (uint32_t vi = t; vi < nvec; vi += NT) {
-        const uint64_t p = gbeg + static_cast<uint64_t>(vi) * VEC;
-        const uint32_t lo = vi * VEC;   // stage index of p
-        if (group_ok && lo >= sh && lo + VEC <= commit + sh) {
-          uint32_t bb;
-          uint64_t off;
-          bucket_of(p, v.log2B, bb, off);
-          __stcs(reinterpret_cast<uint4*>(bk[bb] + off * E), s_stage4[vi]);
-        } else {
-#pragma unroll
-          for (uint32_t e = 0; e < VEC; ++e) {
-            const uint32_t si = lo + e;
-            if (si < sh || si >= commit + sh) continue;
-            uint32_t bb;
-            uint64_t off;
-            bucket_of(p + e, v.log2B, bb, off);
-            store_elem<E>(bk[bb] + off * E, s_stage[si]);
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (t == 0) s_base = base + commit;
-    const int stop = s_stop;
-    __syncthreads();
-    if (stop) break;
-  }
+  __shared__ GenShared sh;
+  grow_passes<E, K, 1>(v, g, blockIdx.x, R, ~0ull, sh, s_stage4, kGenStageBytes / E);
 }
 
 int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32_t R, uint32_t* /*done*/,
