@@ -44,13 +44,19 @@ __device__ __forceinline__ uint32_t warp_scan_packed(uint32_t v) {
 }
 
 constexpr int kSpawnP = 8;   // parents per thread per pass (coarsening)
+// Children of a pass staged in shared memory (a pass of 512 threads averages
+// 4096 children, 64 KB) and written with coalesced 16-byte stores; a pass
+// with more children than the stage holds writes them directly.
+constexpr uint32_t kSpawnStage = 5120;
 
 // One block per LFVector.  Parents of a pass are j = c0 + p*NT + t (p < P),
 // so the block reads them coalesced and their order is (p, t): the same
 // round-major order the packed two-counter scan produces.
-__global__ void __launch_bounds__(1024) spawn_kernel(ArrayView v, uint32_t gen, uint64_t seed, int only_newborn,
-                                                     uint64_t* born) {
+template <int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t gen, uint64_t seed, int only_newborn,
+                                                           uint64_t* born) {
   constexpr int KP = kSpawnP / 2;
+  extern __shared__ uint4 s_kids[];   // kSpawnStage children
   __shared__ uint32_t s_wt[KP][32];
   __shared__ uint32_t s_rb[kSpawnP + 1];
   __shared__ uint64_t s_base;
@@ -140,6 +146,7 @@ __global__ void __launch_bounds__(1024) spawn_kernel(ArrayView v, uint32_t gen, 
 
     const uint64_t base = s_base;
     const uint32_t commit = s_commit;
+    const bool staged = commit <= kSpawnStage;
 #pragma unroll
     for (int j2 = 0; j2 < KP; ++j2) {
       const uint32_t ex = s_wt[j2][warp] + inc[j2] - pk[j2];
@@ -156,11 +163,24 @@ __global__ void __launch_bounds__(1024) spawn_kernel(ArrayView v, uint32_t gen, 
           uint4 child = rec[p];
           child.x = static_cast<uint32_t>(id);
           child.y = static_cast<uint32_t>(id >> 32);
-          uint32_t bb;
-          uint64_t off;
-          bucket_of(local, v.log2B, bb, off);
-          __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16), child);
+          if (staged) {
+            s_kids[q] = child;
+          } else {
+            uint32_t bb;
+            uint64_t off;
+            bucket_of(local, v.log2B, bb, off);
+            __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16), child);
+          }
         }
+      }
+    }
+    __syncthreads();
+    if (staged) {
+      for (uint32_t q = t; q < commit; q += NT) {
+        uint32_t bb;
+        uint64_t off;
+        bucket_of(base + q, v.log2B, bb, off);
+        __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16), s_kids[q]);
       }
     }
     __syncthreads();
@@ -196,7 +216,14 @@ __global__ void __launch_bounds__(256) work_pass_kernel(uint4* __restrict__ rec,
 int launch_twophase_spawn(const ArrayView& v, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born,
                           cudaStream_t st) {
   const uint32_t NT = (v.T + 31) / 32 * 32;
-  spawn_kernel<<<v.L, NT, 0, st>>>(v, gen, seed, only_newborn, born);
+  const int smem = static_cast<int>(kSpawnStage * 16);
+  if (NT <= 512) {
+    cudaFuncSetAttribute(spawn_kernel<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    spawn_kernel<512, 2><<<v.L, NT, smem, st>>>(v, gen, seed, only_newborn, born);
+  } else {
+    cudaFuncSetAttribute(spawn_kernel<1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    spawn_kernel<1024, 1><<<v.L, NT, smem, st>>>(v, gen, seed, only_newborn, born);
+  }
   if (cudaGetLastError() != cudaSuccess) return GGA_ERR_CUDA;
   return launch_finalize(v, st);
 }
