@@ -198,6 +198,7 @@ class Server:
         waiting = []                                # (arrival, request): heads that are appends not fitting yet
         wait_cls = {}                               # their bucket classes (fixed while they wait)
         freed = 0                                   # counts frees of pool memory (flattens)
+        t_full = math.inf                           # arrival time of the first append that did not fit
         checked = 0                                 # value of `freed` when `waiting` was last tried
         nxt = 0
         inflight = deque()                          # (event, [requests], result locations, slot)
@@ -280,6 +281,7 @@ class Server:
                     else:
                         wait_cls[r] = cls
                         heapq.heappush(waiting, (t_arr[r], r))
+                        t_full = min(t_full, t_arr[r])
                     continue
                 if typ[r] == READ:
                     reads.append(r)
@@ -309,6 +311,15 @@ class Server:
         wall = time.perf_counter() - t0
         self.latency, self.state = lat, state
         rep = self._report(lat, state, typ, nn, wall, appended)
+        # The same latencies split at the first append the pool could not hold:
+        # before it the server is bound by its own work, after it by memory.
+        rep["pool_first_full_s"] = None if math.isinf(t_full) else round(float(t_full), 3)
+        for name, sel in (("before_pool_full", t_arr < t_full), ("after_pool_full", t_arr >= t_full)):
+            done = (state == 1) & sel
+            if done.any():
+                ms = lat[done] * 1e3
+                rep[name] = {"completed": int(done.sum()), "p50_ms": round(float(np.percentile(ms, 50)), 4),
+                             "p99_ms": round(float(np.percentile(ms, 99)), 4)}
         rep["steps"] = steps
         rep["mean_requests_per_step"] = round(batched_reqs / max(1, steps), 3)
         return rep
