@@ -54,6 +54,7 @@ def parse_args():
     ap.add_argument("--rounds", type=int, default=512, help="insertion rounds per step (512 = full workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baselines", action="store_true", help="skip the static / semi-static flat arrays")
+    ap.add_argument("--nvtx", action="store_true", help="NVTX range around every phase of a step (for a profiler)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling",
@@ -253,10 +254,17 @@ def run_ours(args, world, rank, local):
 
     phases = ["clear", "insert", "read", "write", "rw_b", "rw_g", "flatten"]
 
+    nvtx = torch.cuda.nvtx if args.nvtx else None
+
     def step(ev=None):
         def mark(i):
             if ev is not None:
                 ev[i].record(stream)
+            if nvtx is not None:
+                if i > 0:
+                    nvtx.range_pop()
+                if i < len(phases):
+                    nvtx.range_push(phases[i])
         mark(0)
         g.clear(stream)
         mark(1)

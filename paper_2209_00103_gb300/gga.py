@@ -38,7 +38,8 @@ EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gg
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
             "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy", "gga_append_batch", "gga_read_batch",
-            "gga_vmm_create", "gga_vmm_grow", "gga_vmm_info", "gga_vmm_destroy", "gga_flat_insert"]
+            "gga_vmm_create", "gga_vmm_grow", "gga_vmm_info", "gga_vmm_destroy", "gga_flat_insert",
+            "gga_debug_wait_timeout"]
 
 
 class gga_params(ctypes.Structure):
@@ -119,6 +120,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_read_batch": [ctypes.POINTER(gga_read_req), u32, vp],
         "gga_twophase_work": [vp, u64, u32, vp],
         "gga_flat_insert": [i32, vp, u64, vp, u64, u32, u32, vp],
+        "gga_debug_wait_timeout": [u32, i32, vp],
         "gga_vmm_create": [u64, ctypes.POINTER(vp)],
         "gga_vmm_grow": [vp, u64],
         "gga_vmm_info": [vp, ctypes.POINTER(u64)],
@@ -332,6 +334,12 @@ def gga_read_batch(reqs, stream=None):
         arr[i].array, arr[i].n, arr[i].seed = g.h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF
         arr[i].out = out.data_ptr()
     _check(load_library().gga_read_batch(arr, len(reqs), _stream(stream)), "gga_read_batch")
+
+
+def gga_debug_wait_timeout(attempts: int, arrive: bool, stream=None) -> int:
+    """Test hook (include/gga_debug.h): status of a bounded mbarrier wait
+    that completes (arrive) or that nothing completes (GGA_ERR_TIMEOUT)."""
+    return int(load_library().gga_debug_wait_timeout(int(attempts), 1 if arrive else 0, _stream(stream)))
 
 
 GGA_FLAT_ATOMIC = 0
