@@ -232,6 +232,53 @@ __device__ inline uint32_t grow_buckets(const ArrayView& v, uint32_t l, uint32_t
   return got;
 }
 
+// grow_buckets by a whole warp (every lane calls it with the same
+// arguments): lane i takes bucket nb + i (+32, ...), so the queue pops of an
+// LFVector's buckets are in flight together instead of one after another;
+// the misses get one bump of the slab for all of them, in bucket order.
+// Same result as grow_buckets (which queued bucket of a class a bucket gets
+// may differ; contents, sizes and capacities do not).
+__device__ inline uint32_t grow_buckets_warp(const ArrayView& v, uint32_t l, uint32_t nb, uint32_t need) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t* tab = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
+  if (need > static_cast<uint32_t>(kMaxBuckets)) need = kMaxBuckets;
+  uint32_t got = nb;
+  bool open = true;   // the allocated prefix has not ended yet
+  for (uint32_t b0 = nb; b0 < need; b0 += 32) {
+    const uint32_t b = b0 + lane;
+    const bool in = b < need;
+    uint64_t a = in ? tab[b] : 0;
+    const bool pop = in && a == 0;
+    const uint64_t sz = pop ? alloc_bytes_for(bucket_len(b, v.log2B) * v.E) : 0;
+    if (pop) a = ring_pop(v.pool, class_of(bucket_len(b, v.log2B) * v.E));
+    const uint64_t mb = (pop && a == 0) ? sz : 0;
+    const uint64_t incl = warp_incl_scan(mb);
+    const uint64_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+      uint64_t off0 = 0;
+      if (lane == 0) off0 = atomicAdd(&v.pool->bump, static_cast<unsigned long long>(total));
+      off0 = __shfl_sync(0xffffffffu, off0, 0);
+      if (mb) {
+        const uint64_t off = off0 + incl - mb;   // bucket order; once one does not fit, none after it does
+        if (off + mb <= v.pool->cap) a = v.pool->base + off;
+      }
+    }
+    if (pop && a) tab[b] = a;
+    const uint32_t present = __ballot_sync(0xffffffffu, in && a != 0);
+    const uint32_t inmask = __ballot_sync(0xffffffffu, in);
+    if (open) {
+      const uint32_t gap = ~present & inmask;
+      if (gap) {
+        got = b0 + static_cast<uint32_t>(__ffs(static_cast<int>(gap)) - 1);
+        open = false;
+      } else {
+        got = b0 + static_cast<uint32_t>(__popc(inmask));
+      }
+    }
+  }
+  return got;
+}
+
 // Chunks of kChunkBytes covering the live part of LFVector of `size`
 // elements, bucket by bucket (flatten / rw_b work units).
 __device__ __forceinline__ uint64_t bucket_chunks(uint64_t size, uint32_t log2B, uint32_t E) {

@@ -198,26 +198,29 @@ __global__ void __launch_bounds__(256) reserve_kernel(ArrayView v, InsertScratch
       }
     }
     __syncwarp();
+    if (lane == 0) pre_l[R] = S;
+    // The whole warp allocates (S and base are the same in every lane).
+    uint32_t nb = 0, need = 0, got = 0;
+    if (S > 0) {
+      nb = v.nbuckets[l];
+      need = buckets_for(base + S, v.log2B);
+      if (need > nb) got = grow_buckets_warp(v, static_cast<uint32_t>(l), nb, need);
+    }
+    __syncwarp();
     if (lane == 0) {
-      pre_l[R] = S;
       uint64_t commit = S;
-      if (S > 0) {
-        const uint32_t nb = v.nbuckets[l];
-        const uint32_t need = buckets_for(base + S, v.log2B);
-        if (need > nb) {
-          const uint32_t got = grow_buckets(v, static_cast<uint32_t>(l), nb, need);
-          v.nbuckets[l] = got;
-          if (got < need) {
-            // Keep the longest prefix of rounds that fits (pool exhausted).
-            const uint64_t cap = bucket_first(got, v.log2B);
-            uint32_t lo = 0, hi = R;  // largest r with base + pre_l[r] <= cap
-            while (lo < hi) {
-              const uint32_t mid = (lo + hi + 1) >> 1;
-              if (base + pre_l[mid] <= cap) lo = mid; else hi = mid - 1;
-            }
-            commit = pre_l[lo];
-            latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
+      if (S > 0 && need > nb) {
+        v.nbuckets[l] = got;
+        if (got < need) {
+          // Keep the longest prefix of rounds that fits (pool exhausted).
+          const uint64_t cap = bucket_first(got, v.log2B);
+          uint32_t lo = 0, hi = R;  // largest r with base + pre_l[r] <= cap
+          while (lo < hi) {
+            const uint32_t mid = (lo + hi + 1) >> 1;
+            if (base + pre_l[mid] <= cap) lo = mid; else hi = mid - 1;
           }
+          commit = pre_l[lo];
+          latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
         }
       }
       s.ins_base[l] = base;
