@@ -219,17 +219,25 @@ int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds
 
 /*
  * gga_read -- out_dev[i] = element at global index idx_dev[i], i < n (rw_g
- * addressing, Sec. VI-B: binary search over the prefix sum of sizes, then the
- * bucket and offset of the LFVector-local index).  idx_dev: uint64 [n];
- * out_dev: n elements of E bytes.  An index >= size latches
- * GGA_ERR_OUT_OF_RANGE and its output element is zeroed.
+ * addressing, Sec. VI-B: search over the prefix sum of sizes -- started from
+ * the proportional guess i * L / N --, then the bucket and offset of the
+ * LFVector-local index).  idx_dev: uint64 [n], 8-byte aligned; out_dev: n
+ * elements of E bytes.  An index >= size latches GGA_ERR_OUT_OF_RANGE and
+ * its output element is zeroed.
  */
 int gga_read(gga_handle h, const uint64_t* idx_dev, uint64_t n, void* out_dev, void* stream);
 
 /*
  * gga_write -- element at global index idx_dev[i] = in_dev[i], i < n.
- * Duplicate indices race (the GPU keeps one of the values); an index >= size
- * latches GGA_ERR_OUT_OF_RANGE and is skipped.
+ * idx_dev: uint64 [n], 8-byte aligned; in_dev: n elements of E bytes,
+ * E-aligned.  Duplicate indices race (the GPU keeps one of the values); an
+ * index >= size latches GGA_ERR_OUT_OF_RANGE and is skipped.  A batch of
+ * 2^20 writes or more is grouped by ranges of global indices first and
+ * applied range by range (the writes that share a 32-byte sector then meet
+ * in L2); its bins, (8 + E) * n + 4 KB bytes of device memory, are allocated
+ * stream-ordered on the first such call and kept by the handle (reused and
+ * grown by later calls, freed by gga_destroy).  If they cannot be allocated
+ * the writes go directly.
  */
 int gga_write(gga_handle h, const uint64_t* idx_dev, uint64_t n, const void* in_dev, void* stream);
 
