@@ -46,8 +46,10 @@ template <int E>
 __device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* stage) {
   const ArrayView& v = J.v;
   const uint64_t target = J.target / v.L + (l < J.target % v.L ? 1 : 0);
-  const uint32_t drawn = grow_passes<E, (E == 16 ? 4 : 8), 2>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
-                                                             kBatchStageBytes / E);
+  // Rounds per pass: a pass of T <= 1024 threads at one element per thread
+  // and round then averages <= 32 KB, inside the 48 KB stage.
+  constexpr int K = E == 4 ? 8 : (E == 8 ? 4 : 2);
+  const uint32_t drawn = grow_passes<E, K, 2>(v, J.g, l, kBatchMaxRounds, target, sh, stage, kBatchStageBytes / E);
   if (threadIdx.x == 0 && sh.stop == 0 && drawn >= kBatchMaxRounds) latch_error(v.status, GGA_ERR_TIMEOUT);
   __syncthreads();
 }

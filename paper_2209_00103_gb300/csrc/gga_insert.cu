@@ -804,16 +804,18 @@ int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32
   const GenParams g = make_gen_params(spec);
   const uint32_t NT = (v.T + 31) / 32 * 32;
   const size_t smem = kGenStageBytes;
-#define GGA_GEN_AS(EE, MT, MB)                                                                               \
+#define GGA_GEN_AS(EE, KK, MT, MB)                                                                           \
   do {                                                                                                       \
-    cudaFuncSetAttribute(gen_insert_kernel<EE, GenK<EE>::value, MT, MB>,                                     \
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));               \
-    gen_insert_kernel<EE, GenK<EE>::value, MT, MB><<<v.L, NT, smem, st>>>(v, g, R);                          \
+    cudaFuncSetAttribute(gen_insert_kernel<EE, KK, MT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                         static_cast<int>(smem));                                                            \
+    gen_insert_kernel<EE, KK, MT, MB><<<v.L, NT, smem, st>>>(v, g, R);                                       \
   } while (0)
+  // Rounds per pass: a pass then averages <= 32 KB at one element per thread
+  // and round (K halves for blocks of more than 512 threads beyond 4 bytes).
 #define GGA_GEN(EE)                                                                                          \
   do {                                                                                                       \
-    if (NT <= 512) GGA_GEN_AS(EE, 512, kGenMinBlocks512);                                                    \
-    else GGA_GEN_AS(EE, 1024, 1);                                                                            \
+    if (NT <= 512) GGA_GEN_AS(EE, GenK<EE>::value, 512, kGenMinBlocks512);                                  \
+    else GGA_GEN_AS(EE, (EE == 4 ? 8 : GenK<EE>::value / 2), 1024, 1);                                       \
   } while (0)
   if (v.E == 4) GGA_GEN(4);
   else if (v.E == 8) GGA_GEN(8);
