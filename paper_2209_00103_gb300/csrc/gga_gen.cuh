@@ -316,11 +316,15 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         }
       }
     }
-    __syncthreads();
+    // No barrier here: the next pass writes the stage, sh.wt, sh.rb and
+    // sh.commit only after its first two barriers, which every thread reaches
+    // after finishing this pass; sh.base is written by thread 0 and read by
+    // thread 0 (the leader) before the next pass's second barrier and by the
+    // others after it; sh.stop was set before this pass's second barrier.
     if (t0 == 0) sh.base = base + commit;
     r0 += kk;
-    __syncthreads();
   }
+  __syncthreads();   // the caller may reuse the stage and sh
   return r0;
 }
 
