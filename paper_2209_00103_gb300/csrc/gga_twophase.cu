@@ -183,11 +183,13 @@ __global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t
         __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16), s_kids[q]);
       }
     }
-    __syncthreads();
+    // No barrier here: the next pass writes the stage and the shared scan
+    // state only after its first two barriers, which every thread reaches
+    // after finishing this pass; s_base is written by thread 0 and read by
+    // thread 0 (the leader) before the next pass's second barrier and by the
+    // others after it; s_stop was set before this pass's second barrier.
     if (t == 0) s_base = base + commit;
-    const int stop = s_stop;
-    __syncthreads();
-    if (stop) break;
+    if (s_stop) break;
   }
   if (t == 0 && only_newborn) born[l] = s;
 }
