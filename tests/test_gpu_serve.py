@@ -124,3 +124,36 @@ def test_server_admission_under_a_full_pool():
     info = srv.pool.info()
     assert info["bump_bytes"] <= cfg.pool_bytes
     srv.close()
+
+
+def test_full_served_configuration_sample_matches_oracle():
+    # One second of the full configuration (65,536 int64 arrays, a 64 GiB
+    # pool, 20k requests/s): every read and flatten of a sample of arrays
+    # equals the oracle's replay of that array's admitted requests in
+    # arrival order.
+    cfg = serving.ServeConfig(duration=1.0)
+    trace = serving.make_trace(cfg)
+    srv = serving.Server(cfg, record=True)
+    rep = srv.run(trace, batched=True)
+    state = srv.state
+    t, typ, arr, nn, tag = trace
+    assert rep["completed"] + rep["rejected"] == len(t) and rep["completed"] > 0
+    res = srv.results
+    srv.close()
+    counts = np.bincount(arr[state == 1], minlength=cfg.n_arrays)
+    sample = np.nonzero(counts >= 2)[0][:48]
+    assert len(sample) >= 16
+    checked = 0
+    for a in sample:
+        o = oracle.OracleGGArray(cfg.L, cfg.T, cfg.B, cfg.E)
+        for r in np.nonzero((arr == a) & (state == 1))[0]:
+            if typ[r] == serving.APPEND:
+                o.append(int(nn[r]), int(tag[r]))
+            elif typ[r] == serving.READ:
+                assert res[r].tobytes() == o.read_random(cfg.read_n, int(tag[r])).view(np.int64).tobytes(), r
+                checked += 1
+            else:
+                assert res[r].tobytes() == o.flatten().view(np.int64).tobytes(), r
+                o = oracle.OracleGGArray(cfg.L, cfg.T, cfg.B, cfg.E)
+                checked += 1
+    assert checked > 0
