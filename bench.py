@@ -71,26 +71,33 @@ def parse_args():
 
 # Source files that define each kernel: a recorded DRAM traffic figure is
 # only used while their hash matches the one stored with it.
+DEVICE_H = "include/gga_device.cuh"
 KERNEL_SOURCES = {
-    "write_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "read_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "flatten_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "sweep_b_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "sweep_g_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "copy_bulk_kernel": ["gga_insert.cu", "gga_core.cuh", "gga_gen.cuh"],
-    "count_kernel": ["gga_insert.cu", "gga_core.cuh", "gga_gen.cuh"],
-    "wbin_count_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "wbin_scatter_kernel": ["gga_access.cu", "gga_core.cuh"],
-    "wbin_apply_kernel": ["gga_access.cu", "gga_core.cuh"],
+    "write_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "read_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "flatten_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "sweep_b_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "sweep_g_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "copy_bulk_kernel": ["gga_insert.cu", "gga_core.cuh", "gga_gen.cuh", DEVICE_H],
+    "count_kernel": ["gga_insert.cu", "gga_core.cuh", "gga_gen.cuh", DEVICE_H],
+    "wbin_count_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "wbin_scatter_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
+    "wbin_apply_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_paper_growth_1024x512_B4096_R512.md")
+
+
+def kernel_source_path(f: str) -> str:
+    """A KERNEL_SOURCES entry: a path from the repository root for the public
+    headers, else a file of the package's csrc/."""
+    return os.path.join(ROOT, f) if f.startswith("include/") else os.path.join(ROOT, "paper_2209_00103_gb300", "csrc", f)
 
 
 def kernel_source_sha(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(kernel, []):
-        with open(os.path.join(ROOT, "paper_2209_00103_gb300", "csrc", f), "rb") as fh:
+        with open(kernel_source_path(f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
@@ -362,8 +369,10 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world, dev, stream)
 
-    # In-kernel generated insertion (values drawn by the inserting threads).
+    # In-kernel generated insertion (values drawn by the inserting threads):
+    # rounds batched in passes, and the device API's one push per round.
     gen = time_generated(w, R, pool_bytes, dev, stream)
+    push_gen = time_generated(w, R, pool_bytes, dev, stream, per_round=True)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world, "steps": K,
@@ -383,6 +392,7 @@ def run_ours(args, world, rank, local):
         "mem_over_needed": round(mem["bucket_bytes"] / max(1, mem["live_bytes"]), 4),
         "memory": mem,
         "insert_generated": gen,
+        "push_generated": push_gen,
         "gpu_launches": K * (sum(LAUNCHES_PER_STEP.values()) - (0 if binned else 3)),
         "clocks": clocks,
         "e2e": e2e,
@@ -570,13 +580,17 @@ def run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world,
             "pipelining": "double-buffered inputs/outputs, uploads and downloads on their own streams"}
 
 
-def time_generated(w, R, pool_bytes, dev, stream):
+def time_generated(w, R, pool_bytes, dev, stream, per_round=False):
+    """The generated insertion of the workload's rounds: gga_insert_generated
+    (rounds batched in passes), or with per_round gga_push_generated (the
+    device API: one gga::block_push_back per round, Algorithm 1 as written)."""
     from paper_2209_00103_gb300 import gga
     g = gga.GGArray(w.L, w.T, w.B, w.E, pool_bytes)
     spec = gga.make_gen_spec(w.spec.seed, w.spec.dist, w.spec.coeffs)
+    run = g.push_generated if per_round else g.insert_generated
     for _ in range(3):
         g.clear(stream)
-        g.insert_generated(spec, R, stream)
+        run(spec, R, stream)
     torch.cuda.synchronize(dev)
     n, rc = g.size(stream)
     K = 10
@@ -584,7 +598,7 @@ def time_generated(w, R, pool_bytes, dev, stream):
     for a, b in evs:
         g.clear(stream)
         a.record(stream)
-        g.insert_generated(spec, R, stream)
+        run(spec, R, stream)
         b.record(stream)
     torch.cuda.synchronize(dev)
     ms = statistics.median(a.elapsed_time(b) for a, b in evs)
@@ -593,7 +607,8 @@ def time_generated(w, R, pool_bytes, dev, stream):
     peak, _ = peaks()
     return {"elements": n, "ms": round(ms, 4), "gelem_s": round(n / (ms / 1e3) / 1e9, 2),
             "achieved_gbs": round(gbs, 1), "frac_of_measured_peak": round(gbs / peak, 3),
-            "device_error": rc, "kernels": "gen_insert_kernel + finalize_kernel",
+            "device_error": rc,
+            "kernels": ("push_generated_kernel" if per_round else "gen_insert_kernel") + " + finalize_kernel",
             "algorithmic_bytes": "E per element (values drawn in registers, write only)"}
 
 

@@ -218,6 +218,35 @@ int gga_reserve(gga_handle h, const uint64_t* target_dev, void* stream);
 int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds, void* stream);
 
 /*
+ * Device API (the paper's model, Sec. III-B and Algorithm 1: push_back is
+ * called by the threads of a block inside a user kernel).  The device side
+ * is the header-only include/gga_device.cuh (gga::block_push_back,
+ * gga::lfv_at, gga::global_at); these calls connect it to a handle.
+ *
+ * gga_device_view -- *view_dev (host) receives a DEVICE pointer to the
+ *  handle's gga_dev_view, to be passed to user kernels as a
+ *  `const gga_dev_view*`.  The pointer stays valid, and its contents fixed,
+ *  until gga_destroy; no stream work.
+ *
+ * gga_device_commit -- enqueue, after the user kernel(s) that pushed into
+ *  the array, the step every insertion ends with: the prefix sum of LFVector
+ *  sizes (Sec. IV) and the global size are recomputed and the pool's queued
+ *  buckets the kernels took are accounted.  Required before any other call
+ *  on the handle, or on another handle of the same pool, that follows the
+ *  pushes.  Errors the kernels found (gga_device.cuh lists them) are latched
+ *  in the handle's status word and returned by gga_last_error / gga_size.
+ *
+ * gga_push_generated -- gga_insert_generated written as a user kernel of
+ *  the device API: one block of T threads per LFVector, one
+ *  gga::block_push_back per round, then gga_device_commit.  Same draws, same
+ *  result, same errors as gga_insert_generated; it is the per-round form of
+ *  Algorithm 1, which gga_insert_generated batches over rounds.
+ */
+int gga_device_view(gga_handle h, const void** view_dev);
+int gga_device_commit(gga_handle h, void* stream);
+int gga_push_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds, void* stream);
+
+/*
  * gga_read -- out_dev[i] = element at global index idx_dev[i], i < n (rw_g
  * addressing, Sec. VI-B: search over the prefix sum of sizes -- started from
  * the proportional guess i * L / N --, then the bucket and offset of the

@@ -229,10 +229,10 @@ uint64_t* handle_serve_records(gga_handle h, uint64_t slots) {
 
 bool handle_parts(gga_handle h, ArrayView* view, InsertScratch* ins, int* device, int* num_sms) {
   if (!h) return false;
-  *view = h->view;
-  *ins = h->ins;
-  *device = h->device;
-  *num_sms = h->num_sms;
+  if (view) *view = h->view;
+  if (ins) *ins = h->ins;
+  if (device) *device = h->device;
+  if (num_sms) *num_sms = h->num_sms;
   return true;
 }
 }  // namespace gga

@@ -33,7 +33,8 @@ DIST = {"bernoulli": 0, "uniform3": 1, "geometric": 2, "poisson": 3}
 MAX_THRESHOLDS = 16
 
 # Every symbol include/gga.h declares.
-EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gga_insert_generated", "gga_read", "gga_write", "gga_sweep",
+EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gga_insert_generated",
+            "gga_device_view", "gga_device_commit", "gga_push_generated", "gga_read", "gga_write", "gga_sweep",
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
@@ -95,6 +96,9 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_insert_noalloc": [vp, vp, u32, vp, u64, vp],
         "gga_insert_generated": [vp, ctypes.POINTER(gga_gen_spec), u32, vp],
         "gga_reserve": [vp, vp, vp],
+        "gga_device_view": [vp, ctypes.POINTER(vp)],
+        "gga_device_commit": [vp, vp],
+        "gga_push_generated": [vp, ctypes.POINTER(gga_gen_spec), u32, vp],
         "gga_read": [vp, vp, u64, vp, vp],
         "gga_write": [vp, vp, u64, vp, vp],
         "gga_sweep": [vp, i32, u64, u32, vp],
@@ -252,6 +256,23 @@ def gga_reserve(h, target: torch.Tensor, stream=None):
 def gga_insert_generated(h, spec: gga_gen_spec, rounds: int, stream=None):
     _check(load_library().gga_insert_generated(h, ctypes.byref(spec), rounds, _stream(stream)),
            "gga_insert_generated")
+
+
+def gga_device_view(h) -> int:
+    """Device address of the handle's gga_dev_view (include/gga_device.cuh),
+    for user kernels that call gga::block_push_back."""
+    v = ctypes.c_void_p()
+    _check(load_library().gga_device_view(h, ctypes.byref(v)), "gga_device_view")
+    return v.value
+
+
+def gga_device_commit(h, stream=None):
+    _check(load_library().gga_device_commit(h, _stream(stream)), "gga_device_commit")
+
+
+def gga_push_generated(h, spec: gga_gen_spec, rounds: int, stream=None):
+    _check(load_library().gga_push_generated(h, ctypes.byref(spec), rounds, _stream(stream)),
+           "gga_push_generated")
 
 
 def gga_read(h, idx: torch.Tensor, out: torch.Tensor, stream=None):
@@ -482,6 +503,18 @@ class GGArray:
 
     def insert_generated(self, spec, rounds, stream=None):
         gga_insert_generated(self.h, spec, rounds, stream)
+
+    def device_view(self) -> int:
+        """Device pointer to pass to user kernels as `const gga_dev_view*`."""
+        return gga_device_view(self.h)
+
+    def device_commit(self, stream=None):
+        """After user kernels pushed into the array (before any other call)."""
+        gga_device_commit(self.h, stream)
+
+    def push_generated(self, spec, rounds, stream=None):
+        """insert_generated through the device API, one block_push_back per round."""
+        gga_push_generated(self.h, spec, rounds, stream)
 
     def read(self, idx, out=None, stream=None):
         if out is None:

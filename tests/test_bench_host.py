@@ -27,7 +27,7 @@ def test_every_kernel_with_sources_hashes_existing_files():
     for k, files in bench.KERNEL_SOURCES.items():
         assert files
         for f in files:
-            assert os.path.exists(os.path.join(bench.ROOT, "paper_2209_00103_gb300", "csrc", f)), (k, f)
+            assert os.path.exists(bench.kernel_source_path(f)), (k, f)
 
 
 def test_algorithmic_bytes_per_unit():
