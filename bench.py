@@ -363,6 +363,15 @@ def run_ours(args, world, rank, local):
     baselines = None
     if not args.no_baselines and rank == 0 and w.E == 4:
         baselines = run_flat_baselines(counts, values, idx_r, idx_w, vals_w, N, R, w.L, w.T, dev, stream)
+        if dom == "read":
+            # A random gather is bound by the DRAM access rate, not by its
+            # bytes: the same indices gathered from a flat int32 array by
+            # PyTorch give the ceiling the translated read is held against.
+            flat_ms = baselines["static"]["phases_ms"]["read"]
+            roofline["vs_flat_gather"] = {
+                "flat_ms": flat_ms, "ms": round(ph_ms["read"], 4), "frac": round(flat_ms / ph_ms["read"], 3),
+                "accesses_per_s": round(n_rand / (ph_ms["read"] / 1e3) / 1e9, 2), "unit": "G accesses/s",
+                "flat": "torch.index_select on a flat int32 array of the same size, same indices"}
 
     # End to end through the C ABI with host buffers.
     e2e = None
