@@ -328,8 +328,9 @@ int gga_last_error(gga_handle h, void* stream);
  * of the child).  Parents are all records present when the call starts
  * (only_newborn = 0), or for only_newborn = 1 the records from born_dev[l]
  * (uint64 [L], device, updated to the size at the start of the call).
- * Device errors as gga_insert (pool exhausted: the LFVector keeps the passes
- * that fit).
+ * Device errors as gga_insert (pool exhausted: the LFVector keeps the
+ * children of its first parents, a multiple of 1024 of them, whose children
+ * fit, and spawns no more in this call).
  */
 int gga_twophase_spawn(gga_handle h, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born_dev,
                        void* stream);

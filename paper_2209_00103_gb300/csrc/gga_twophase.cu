@@ -44,19 +44,21 @@ __device__ __forceinline__ uint32_t warp_scan_packed(uint32_t v) {
 }
 
 constexpr int kSpawnP = 8;   // parents per thread per pass (coarsening)
-// Children of a pass staged in shared memory (a pass of 512 threads averages
-// 4096 children, 64 KB) and written with coalesced 16-byte stores; a pass
-// with more children than the stage holds writes them directly.
-constexpr uint32_t kSpawnStage = 5120;
 
 // One block per LFVector.  Parents of a pass are j = c0 + p*NT + t (p < P),
 // so the block reads them coalesced and their order is (p, t): the same
-// round-major order the packed two-counter scan produces.
+// round-major order the packed two-counter scan produces.  The children of
+// round p of a warp form one run of the LFVector; the warp writes that run
+// cooperatively, lane i taking children i, i+32, ...: the lane finds the
+// child's parent (the last lane whose exclusive count is <= i, a five-step
+// shuffle search), takes the parent's pos and vel by shuffle and stores the
+// child at its bucket position.  Consecutive lanes store consecutive
+// children, so the stores are coalesced without a shared-memory stage, and
+// no lane loops over a long run of its own.
 template <int MAXT, int MINB>
 __global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t gen, uint64_t seed, int only_newborn,
                                                            uint64_t* born) {
   constexpr int KP = kSpawnP / 2;
-  extern __shared__ uint4 s_kids[];   // kSpawnStage children
   __shared__ uint32_t s_wt[KP][32];
   __shared__ uint32_t s_rb[kSpawnP + 1];
   __shared__ uint64_t s_base;
@@ -69,6 +71,7 @@ __global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t
   const uint64_t s = v.sizes[l];                       // parents end here
   const uint64_t first = only_newborn ? born[l] : 0;   // ... and start here
   const uint64_t goff = v.offsets[l];                  // global index of local 0 at generation start
+  const uint64_t id_hi = (static_cast<uint64_t>(gen + 1) << 56) | (static_cast<uint64_t>(l) << 40);
   if (t == 0) {
     s_base = s;
     s_nb = v.nbuckets[l];
@@ -77,7 +80,7 @@ __global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t
   __syncthreads();
 
   for (uint64_t c0 = first; c0 < s; c0 += static_cast<uint64_t>(NT) * kSpawnP) {
-    uint4 rec[kSpawnP];
+    uint2 pv[kSpawnP];   // parents' pos and vel (the children's copy)
     uint32_t pk[KP], inc[KP];
 #pragma unroll
     for (int j2 = 0; j2 < KP; ++j2) {
@@ -87,12 +90,13 @@ __global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t
         const int p = 2 * j2 + h;
         const uint64_t j = c0 + static_cast<uint64_t>(p) * NT + t;
         c[h] = 0;
-        rec[p] = make_uint4(0, 0, 0, 0);
+        pv[p] = make_uint2(0, 0);
         if (j < s) {
           uint32_t bb;
           uint64_t off;
           bucket_of(j, v.log2B, bb, off);
-          rec[p] = *reinterpret_cast<const uint4*>(bk[bb] + off * 16);
+          const uint4 rec = *reinterpret_cast<const uint4*>(bk[bb] + off * 16);
+          pv[p] = make_uint2(rec.z, rec.w);
           c[h] = trailing_ones(splitmix2(seed, (static_cast<uint64_t>(gen) << 48) | (goff + j)));
         }
       }
@@ -146,48 +150,48 @@ __global__ void __launch_bounds__(MAXT, MINB) spawn_kernel(ArrayView v, uint32_t
 
     const uint64_t base = s_base;
     const uint32_t commit = s_commit;
-    const bool staged = commit <= kSpawnStage;
 #pragma unroll
     for (int j2 = 0; j2 < KP; ++j2) {
-      const uint32_t ex = s_wt[j2][warp] + inc[j2] - pk[j2];
+      const uint32_t wo = s_wt[j2][warp];                       // the warp's offset in rounds 2j2, 2j2+1
+      const uint32_t ex = inc[j2] - pk[j2];                     // the lane's, inside the warp
+      const uint32_t wt = __shfl_sync(0xffffffffu, inc[j2], 31);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = 2 * j2 + h;
-        const uint32_t c = (pk[j2] >> (16 * h)) & 0xFFFFu;
-        const uint32_t st = s_rb[p] + ((ex >> (16 * h)) & 0xFFFFu);
-        for (uint32_t k = 0; k < c; ++k) {
-          const uint32_t q = st + k;
-          if (q >= commit) break;
-          const uint64_t local = base + q;
-          const uint64_t id = (static_cast<uint64_t>(gen + 1) << 56) | (static_cast<uint64_t>(l) << 40) | local;
-          uint4 child = rec[p];
-          child.x = static_cast<uint32_t>(id);
-          child.y = static_cast<uint32_t>(id >> 32);
-          if (staged) {
-            s_kids[q] = child;
-          } else {
+        const uint32_t exl = (ex >> (16 * h)) & 0xFFFFu;
+        const uint32_t wtot = (wt >> (16 * h)) & 0xFFFFu;
+        const uint32_t q0 = s_rb[p] + ((wo >> (16 * h)) & 0xFFFFu);   // block position of the warp's run
+        for (uint32_t i0 = 0; i0 < wtot; i0 += 32) {
+          const uint32_t q = i0 + lane;
+          uint32_t src = 0;
+#pragma unroll
+          for (uint32_t step = 16; step > 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, exl, src + step);
+            if (e <= q) src += step;
+          }
+          const uint32_t pos = __shfl_sync(0xffffffffu, pv[p].x, src);
+          const uint32_t vel = __shfl_sync(0xffffffffu, pv[p].y, src);
+          if (q < wtot && q0 + q < commit) {
+            const uint64_t local = base + q0 + q;
+            const uint64_t id = id_hi | local;
             uint32_t bb;
             uint64_t off;
             bucket_of(local, v.log2B, bb, off);
-            __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16), child);
+            __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16),
+                   make_uint4(static_cast<uint32_t>(id), static_cast<uint32_t>(id >> 32), pos, vel));
           }
         }
       }
     }
-    __syncthreads();
-    if (staged) {
-      for (uint32_t q = t; q < commit; q += NT) {
-        uint32_t bb;
-        uint64_t off;
-        bucket_of(base + q, v.log2B, bb, off);
-        __stcs(reinterpret_cast<uint4*>(bk[bb] + off * 16), s_kids[q]);
-      }
-    }
-    // No barrier here: the next pass writes the stage and the shared scan
-    // state only after its first two barriers, which every thread reaches
-    // after finishing this pass; s_base is written by thread 0 and read by
-    // thread 0 (the leader) before the next pass's second barrier and by the
-    // others after it; s_stop was set before this pass's second barrier.
+    // No block barrier here: the next pass writes s_rb, s_commit and the
+    // warp-offset entries of s_wt only after its first barrier, which every
+    // thread reaches after finishing this pass; the one entry a warp writes
+    // before that barrier (lane 31: s_wt[.][warp]) is its own, read by its
+    // lanes above (the warp synchronizes first).  s_base is written by
+    // thread 0 and read by thread 0 (the leader) before the next pass's
+    // second barrier and by the others after it; s_stop was set before this
+    // pass's second barrier.
+    __syncwarp();
     if (t == 0) s_base = base + commit;
     if (s_stop) break;
   }
@@ -217,15 +221,11 @@ __global__ void __launch_bounds__(256) work_pass_kernel(uint4* __restrict__ rec,
 
 int launch_twophase_spawn(const ArrayView& v, uint32_t gen, uint64_t seed, int only_newborn, uint64_t* born,
                           cudaStream_t st) {
-  const uint32_t NT = (v.T + 31) / 32 * 32;
-  const int smem = static_cast<int>(kSpawnStage * 16);
-  if (NT <= 512) {
-    cudaFuncSetAttribute(spawn_kernel<512, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    spawn_kernel<512, 2><<<v.L, NT, smem, st>>>(v, gen, seed, only_newborn, born);
-  } else {
-    cudaFuncSetAttribute(spawn_kernel<1024, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    spawn_kernel<1024, 1><<<v.L, NT, smem, st>>>(v, gen, seed, only_newborn, born);
-  }
+  // The children's order and values depend on parent indices only, so the
+  // block size is free: 1024 threads, one block per SM, whatever T is.
+  // With 1024 LFVectors that is 6.7 waves of blocks (7 rounds), against 3.4
+  // (4 rounds) with two 512-thread blocks per SM.
+  spawn_kernel<1024, 1><<<v.L, 1024, 0, st>>>(v, gen, seed, only_newborn, born);
   if (cudaGetLastError() != cudaSuccess) return GGA_ERR_CUDA;
   return launch_finalize(v, st);
 }
