@@ -64,6 +64,8 @@ def parse_args():
                          "served: continuous-batching request server")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of offered load")
     ap.add_argument("--newborn", action="store_true", help="two_phase: only the previous generation spawns")
+    ap.add_argument("--n0", type=int, default=1 << 24, help="two_phase: initial records (a smaller case for profiling)")
+    ap.add_argument("--generations", type=int, default=8, help="two_phase: spawning generations")
     ap.add_argument("--deadline", type=float, default=None,
                     help="served: seconds an append may wait for pool memory before it is rejected")
     return ap.parse_args()
@@ -71,6 +73,7 @@ def parse_args():
 
 # Source files that define each kernel: a recorded DRAM traffic figure is
 # only used while their hash matches the one stored with it.
+SECTOR_BYTES = 32   # DRAM/L2 sector: the least a random element access moves
 DEVICE_H = "include/gga_device.cuh"
 KERNEL_SOURCES = {
     "write_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
@@ -333,6 +336,12 @@ def run_ours(args, world, rank, local):
                       "frac_of_measured_peak": round(gbs / peak, 3), "frac_of_8tbs": round(gbs / 8000.0, 3)})
         if name == "insert":
             d["gelem_s"] = round(N / (ph_ms[name] / 1e3) / 1e9, 2)
+        if name in ("read", "write"):
+            # Sector-effective: an element access moves at least one 32-byte
+            # sector, so each access counts index + sector + the other side.
+            sec = n_rand * (8 + SECTOR_BYTES + w.E)
+            d["sector_effective_gbs"] = round(sec / (ph_ms[name] / 1e3) / 1e9, 1)
+            d["sector_effective_frac"] = round(sec / (ph_ms[name] / 1e3) / 1e9 / peak, 3)
         phase_info[name] = d
 
     # The dominant kernel carries the roofline record: the longest phase that
@@ -783,7 +792,7 @@ def run_two_phase(args, world, rank, local):
     import numpy as np
     from paper_2209_00103_gb300 import gga
     from paper_2209_00103_gb300 import workloads as wl
-    w = wl.two_phase(only_newborn=args.newborn)
+    w = wl.two_phase(only_newborn=args.newborn, n0=args.n0, generations=args.generations)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     counts = torch.from_numpy(wl.split_counts(w.L, w.T, w.n0).view(np.int32)).to(dev)
