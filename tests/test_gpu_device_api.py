@@ -281,3 +281,66 @@ def test_push_generated_equals_batched_insert_at_the_paper_growth_size():
     assert torch.equal(sa, sb) and torch.equal(ca, cb)
     assert torch.equal(fa[:na], b.flatten()[:nb])
     b.close()
+
+
+def test_user_pushes_and_commit_replay_from_a_cuda_graph(user):
+    # The user kernel and gga_device_commit captured once in a CUDA graph
+    # (no host step between them) and replayed: every replay appends the same
+    # rounds again, as that many insertions of them would.
+    rng = np.random.default_rng(12)
+    L, T, B, E, kmax = 24, 128, 16, 4, 3
+    g, o = make_pair(L, T, B, E, pool_bytes=64 << 20)
+    counts, vals, packed = padded_rounds(rng, 4, L, T, kmax, E, seed=12)
+    cd, vd = counts_to_dev(counts), values_to_dev(vals, E)
+    first = torch.empty(counts.size, dtype=torch.int64, device="cuda")
+    view = g.device_view()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        rc = user.user_push_rounds(ctypes.c_void_p(view), ctypes.c_void_p(cd.data_ptr()),
+                                   ctypes.c_void_p(vd.data_ptr()), ctypes.c_void_p(first.data_ptr()), 4, L, T, 1,
+                                   kmax, E, L, 0, 1, ctypes.c_void_p(s.cuda_stream))
+        g.device_commit(stream=s)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert g.size()[0] == 0   # capture ran nothing
+    for rep in range(3):
+        graph.replay()
+        torch.cuda.synchronize()
+        o.insert(counts, packed)
+        assert g.last_error() == gga.GGA_OK
+        assert_same_state(g, o)
+    g.close()
+
+
+def test_push_generated_pool_exhaustion_keeps_whole_leading_rounds():
+    # A pool too small for the rounds: each LFVector keeps the rounds before
+    # its first failing one (the oracle, run round by round, gives the round
+    # boundaries) and GGA_ERR_POOL_EXHAUSTED is latched.
+    L, T, B, E, R = 12, 64, 16, 4, 20
+    coeffs = (10, 1 << 20, 1 << 19)
+    o = oracle.OracleGGArray(L, T, B, E)
+    bounds = [np.zeros(L, np.int64)]
+    for r in range(R):
+        o.insert_generated(7, "uniform3", coeffs, r, 1)
+        bounds.append(o.sizes().astype(np.int64))
+    full = o.flatten()
+    offs = o.offsets().astype(np.int64)
+    g = gga.GGArray(L, T, B, E, 48 << 10)
+    g.push_generated(gga.make_gen_spec(7, "uniform3", coeffs), R)
+    n, rc, sizes, caps = g.sizes_caps()
+    assert rc == gga.GGA_ERR_POOL_EXHAUSTED
+    sizes = sizes.cpu().numpy()
+    assert np.all(sizes <= caps.cpu().numpy())
+    flat = dev_to_np(g.flatten(), E)[:n]
+    got_offs = np.concatenate([[0], np.cumsum(sizes)])
+    short = 0
+    for l in range(L):
+        kept = [int(b[l]) for b in bounds]
+        assert int(sizes[l]) in kept, l                       # whole rounds only
+        want = full[offs[l]:offs[l] + sizes[l]]
+        assert flat[got_offs[l]:got_offs[l + 1]].tobytes() == want.tobytes(), l
+        short += int(sizes[l]) < kept[-1]
+    assert short > 0
+    g.close()
