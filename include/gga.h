@@ -237,8 +237,8 @@ int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds
  *  in the handle's status word and returned by gga_last_error / gga_size.
  *
  * gga_push_generated -- gga_insert_generated written as a user kernel of
- *  the device API: one block of T threads per LFVector, one
- *  gga::block_push_back per round, then gga_device_commit.  Same draws, same
+ *  the device API: one block of T threads per LFVector, one push per round
+ *  through a gga::BlockPusher, then gga_device_commit.  Same draws, same
  *  result, same errors as gga_insert_generated; it is the per-round form of
  *  Algorithm 1, which gga_insert_generated batches over rounds.
  */

@@ -20,6 +20,11 @@
 //          k<<<L, T, 0, s>>>((const gga_dev_view*)v, ...);
 //          gga_device_commit(h, s);                   // before any other call on h
 //
+// For many pushes into one LFVector in one kernel, gga::BlockPusher keeps
+// the LFVector's size in every thread and needs one block barrier per push
+// (two when the push reaches new buckets), against two for each
+// block_push_back call.
+//
 // Rules (the paper's phase separation, Sec. VI):
 //  - every thread of the block calls block_push_back with the same
 //    LFVector l (it holds two block barriers); l < L;
@@ -404,6 +409,182 @@ template <class T, class F>
 __device__ bool block_push_back(const ArrayView* view, uint32_t count, F value_of_k, uint64_t* first = nullptr) {
   return block_push_back<T>(view, blockIdx.x, count, value_of_k, first);
 }
+
+// Capacity of the first nb buckets, B (2^nb - 1), saturating at 2^64 - 1.
+__host__ __device__ __forceinline__ uint64_t prefix_capacity(uint32_t nb, uint32_t log2B) {
+  return nb + log2B >= 64u ? ~0ull : bucket_first(nb, log2B);
+}
+
+// Shared memory of one BlockPusher (declare it __shared__, one per pusher).
+struct PushShared {
+  unsigned long long warp[2][32];   // warp totals, by call parity
+  uint32_t nb[2];                   // allocated buckets after an allocating call
+  uint32_t ok[2];                   // whether that call's buckets fit
+};
+
+// A block's cursor on one LFVector for many pushes in one kernel: the same
+// appends as calling block_push_back once per push, with the LFVector's size
+// and allocated capacity kept by every thread instead of re-read, and the
+// shared scan slots alternating between calls, so a push that fits in the
+// allocated buckets costs one block barrier; a push that reaches new
+// buckets takes a second one (warp 0 allocates them, Algorithm 2).  Every
+// thread of the block constructs it and calls push with the same sequence
+// of calls.  While it is in use, the block pushes into LFVector l only
+// through it (block_push_back on l would not be seen by the cursor).
+//
+//   __shared__ gga::PushShared sh;
+//   gga::BlockPusher<uint32_t> p(view, l, sh);
+//   for (...) p.push(count, [&](uint32_t k) { return value(k); });
+template <class T>
+struct BlockPusher {
+  const ArrayView* view;
+  PushShared* sh;
+  uint64_t size, cap;
+  uint32_t l, nb, par;
+  bool valid;
+
+  __device__ BlockPusher(const ArrayView* v, uint32_t lfv, PushShared& s)
+      : view(v), sh(&s), size(0), cap(0), l(lfv), nb(0), par(0) {
+    __syncthreads();   // this block's earlier writes to the LFVector are visible
+    valid = lfv < v->L && sizeof(T) == v->E;
+    if (!valid) {
+      if (block_rank() == 0) latch_error(v->status, GGA_ERR_INVALID);
+      return;
+    }
+    size = v->sizes[lfv];
+    nb = v->nbuckets[lfv];
+    cap = prefix_capacity(nb, v->log2B);
+  }
+
+  // Append count elements value_of_k(0..count-1) of this thread after those
+  // of threads 0..t-1 of this call (block_push_back's order).  Returns true
+  // (in every thread) when the block's elements were appended.
+  template <class F>
+  __device__ bool push(uint32_t count, F value_of_k, uint64_t* first = nullptr) {
+    if (!valid) return false;
+    const ArrayView& v = *view;
+    const uint32_t nt = block_threads(), t = block_rank();
+    const uint32_t lane = t & 31, w = t >> 5, nw = (nt + 31) >> 5;
+    const uint32_t in_warp = nt - (w << 5) < 32 ? nt - (w << 5) : 32;
+    const uint32_t mask = in_warp == 32 ? 0xffffffffu : (1u << in_warp) - 1u;
+    const uint32_t pb = par;
+    par ^= 1u;
+
+    // 1. Warp scan of the counts (32-bit while a warp's sum cannot wrap).
+    uint64_t x;
+    if (__all_sync(mask, count < (1u << 26))) {
+      uint32_t y = count;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(mask, y, o);
+        if (lane >= o) y += n;
+      }
+      x = y;
+    } else {
+      x = count;
+#pragma unroll
+      for (uint32_t o = 1; o < 32; o <<= 1) {
+        const uint64_t n = __shfl_up_sync(mask, x, o);
+        if (lane >= o) x += n;
+      }
+    }
+    if (lane == in_warp - 1) sh->warp[pb][w] = x;
+    __syncthreads();
+
+    // 2. Every warp: the block total and its own offset from the warp totals.
+    uint64_t total = 0, woff = 0;
+    if (in_warp == 32) {
+      const uint64_t y = lane < nw ? sh->warp[pb][lane] : 0;
+      if (__all_sync(0xffffffffu, y < (1ull << 26))) {   // 32 of them cannot wrap 32 bits
+        const uint32_t y32 = static_cast<uint32_t>(y);
+        uint32_t yi = y32;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+          const uint32_t n = __shfl_up_sync(0xffffffffu, yi, o);
+          if (lane >= o) yi += n;
+        }
+        total = __shfl_sync(0xffffffffu, yi, 31);
+        woff = __shfl_sync(0xffffffffu, yi - y32, w);
+      } else {
+        uint64_t yi = y;
+#pragma unroll
+        for (uint32_t o = 1; o < 32; o <<= 1) {
+          const uint64_t n = __shfl_up_sync(0xffffffffu, yi, o);
+          if (lane >= o) yi += n;
+        }
+        total = __shfl_sync(0xffffffffu, yi, 31);
+        woff = __shfl_sync(0xffffffffu, yi - y, w);
+      }
+    } else {
+      for (uint32_t i = 0; i < nw; ++i) {
+        const uint64_t y = sh->warp[pb][i];
+        total += y;
+        if (i < w) woff += y;
+      }
+    }
+
+    // 3. Reservation.  All threads hold the same size and capacity, so they
+    //    take the same branch.
+    const uint64_t base = size;
+    const uint64_t end = base + total;
+    bool ok = true;
+    if (end <= cap && end >= base) {
+      size = end;
+      if (t == 0 && total > 0) v.sizes[l] = end;
+    } else {
+      if (w == 0) {
+        const uint32_t need = end < base ? kMaxBuckets + 1u : buckets_for(end, v.log2B);
+        uint32_t got;
+        if (mask == 0xffffffffu && (blockDim.x & 31) == 0) {
+          got = grow_buckets_warp(v, l, nb, need);
+        } else {
+          got = 0;
+          if (lane == 0) got = grow_buckets(v, l, nb, need);
+          got = __shfl_sync(mask, got, 0);
+        }
+        if (lane == 0) {
+          const bool fits = got >= need;
+          v.nbuckets[l] = got;
+          if (fits) v.sizes[l] = end;
+          else latch_error(v.status, GGA_ERR_POOL_EXHAUSTED);
+          sh->nb[pb] = got;
+          sh->ok[pb] = fits ? 1u : 0u;
+        }
+      }
+      __syncthreads();   // the buckets exist before any write
+      nb = sh->nb[pb];
+      cap = prefix_capacity(nb, v.log2B);
+      ok = sh->ok[pb] != 0;
+      if (ok) size = end;
+    }
+
+    // 4. Every thread writes its run.
+    const uint64_t j0 = base + woff + (x - count);
+    if (first) *first = j0;
+    if (!ok) return false;
+    if (count > 0) {
+      const uint64_t* tab = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
+      uint32_t b;
+      uint64_t off;
+      bucket_of(j0, v.log2B, b, off);
+      T* p = reinterpret_cast<T*>(tab[b]) + off;
+      uint64_t left = bucket_len(b, v.log2B) - off;
+      for (uint32_t k = 0; k < count; ++k) {
+        if (left == 0) {
+          ++b;
+          p = reinterpret_cast<T*>(tab[b]);
+          left = bucket_len(b, v.log2B);
+        }
+        *p++ = static_cast<T>(value_of_k(k));
+        --left;
+      }
+    }
+    return true;
+  }
+
+  // The LFVector's size as this cursor has it (the same in every thread).
+  __device__ uint64_t lfv_size() const { return size; }
+};
 
 // Size of LFVector l (after the pushes of earlier calls in this kernel by
 // the same block, or of earlier kernels).

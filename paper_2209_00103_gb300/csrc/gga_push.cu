@@ -1,28 +1,31 @@
 // gga_push.cu -- the device API's own entry points: the view a user kernel
 // pushes through, the commit that follows such a kernel, and the generated
 // insertion written as a user kernel would write it (Algorithm 1 as the
-// paper states it: one block per LFVector, one block_push_back per round).
+// paper states it: one block per LFVector, one push per round, through the
+// device API's BlockPusher).
 #include "gga_core.cuh"
 #include "gga_gen.cuh"
 
 namespace gga {
 
 // Block l draws round r's counts and values exactly as gga_insert_generated
-// does (SplitMix64 on ((r << 32) | l*T + t)), and appends them with one
-// block_push_back per round.  A round that does not fit ends the block's
-// rounds (the rounds that fit are kept, as in every insertion).
+// does (SplitMix64 on ((r << 32) | l*T + t)), and appends them with one push
+// per round through a BlockPusher on LFVector l.  A round that does not fit
+// ends the block's rounds (the rounds that fit are kept, as in every
+// insertion).
 template <int E>
 __global__ void __launch_bounds__(1024) push_generated_kernel(const ArrayView* view, GenParams g, uint32_t R) {
   typedef typename Elem<E>::T T;
+  __shared__ PushShared sh;
   const uint32_t l = blockIdx.x;
   const uint64_t gtid = static_cast<uint64_t>(l) * blockDim.x + threadIdx.x;
+  BlockPusher<T> pusher(view, l, sh);
 #pragma unroll 1
   for (uint32_t i = 0; i < R; ++i) {
     const uint64_t r = static_cast<uint64_t>(g.round0) + i;
     const uint32_t c = gen_count(g, splitmix(g.seed, (r << 32) | gtid));
     const uint64_t v0 = g.va * gtid + g.vb * r;
-    const bool ok = block_push_back<T>(view, l, c, [&](uint32_t k) { return gen_value<E>(v0 + g.vc * k); });
-    if (!ok) break;
+    if (!pusher.push(c, [&](uint32_t k) { return gen_value<E>(v0 + g.vc * k); })) break;
   }
 }
 

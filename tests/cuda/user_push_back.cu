@@ -32,6 +32,51 @@ __global__ void push_rounds(const gga_dev_view* v, const uint32_t* counts, const
   }
 }
 
+// The same rounds through a BlockPusher per LFVector (one shared slot set,
+// reused by the block's successive cursors).
+template <class T>
+__global__ void push_rounds_cursor(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint64_t* first,
+                                   uint32_t R, uint32_t L, uint32_t NT, uint32_t kmax, int reverse, int stop_on_fail) {
+  __shared__ gga::PushShared sh;
+  const uint32_t t = gga::block_rank();
+  for (uint32_t i = blockIdx.x; i < L; i += gridDim.x) {
+    const uint32_t l = reverse ? L - 1 - i : i;
+    gga::BlockPusher<T> pusher(v, l, sh);
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint64_t row = (static_cast<uint64_t>(r) * L + l) * NT + t;
+      const uint32_t c = counts[row];
+      const T* mine = vals + row * kmax;
+      uint64_t j0 = ~0ull;
+      const bool ok = pusher.push(c, [&](uint32_t k) { return mine[k]; }, &j0);
+      first[row] = ok ? j0 : ~0ull;
+      if (!ok && stop_on_fail) break;
+    }
+  }
+}
+
+// Rounds whose values are a formula of (round, LFVector, thread, k), for
+// counts too large to hold their values in an array: element k of thread t
+// of LFVector l in round r is (r << 56) | (l << 48) | (t << 32) | k.
+__global__ void push_formula(const gga_dev_view* v, const uint32_t* counts, uint32_t R, uint32_t L, uint32_t NT,
+                             int cursor) {
+  __shared__ gga::PushShared sh;
+  const uint32_t t = gga::block_rank();
+  const uint32_t l = blockIdx.x;
+  const auto value = [&](uint32_t r) {
+    return [=](uint32_t k) {
+      return (static_cast<unsigned long long>(r) << 56) | (static_cast<unsigned long long>(l) << 48) |
+             (static_cast<unsigned long long>(t) << 32) | k;
+    };
+  };
+  if (cursor) {
+    gga::BlockPusher<unsigned long long> pusher(v, l, sh);
+    for (uint32_t r = 0; r < R; ++r) pusher.push(counts[(static_cast<uint64_t>(r) * L + l) * NT + t], value(r));
+  } else {
+    for (uint32_t r = 0; r < R; ++r)
+      gga::block_push_back<unsigned long long>(v, l, counts[(static_cast<uint64_t>(r) * L + l) * NT + t], value(r));
+  }
+}
+
 // One LFVector per block, the short form (l = blockIdx.x), one round.
 template <class T>
 __global__ void push_own(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint32_t kmax) {
@@ -89,6 +134,32 @@ int user_push_rounds(const void* view, const uint32_t* counts, const void* vals,
   else
     push_rounds<uint4><<<blocks, block, 0, st>>>(v, counts, static_cast<const uint4*>(vals), first, R, L, nt, kmax,
                                                  reverse, stop_on_fail);
+  return launched();
+}
+
+int user_push_rounds_cursor(const void* view, const uint32_t* counts, const void* vals, uint64_t* first, uint32_t R,
+                            uint32_t L, uint32_t bx, uint32_t by, uint32_t kmax, uint32_t E, uint32_t blocks,
+                            int reverse, int stop_on_fail, void* stream) {
+  const gga_dev_view* v = static_cast<const gga_dev_view*>(view);
+  const dim3 block(bx, by);
+  const uint32_t nt = bx * by;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (E == 4)
+    push_rounds_cursor<uint32_t><<<blocks, block, 0, st>>>(v, counts, static_cast<const uint32_t*>(vals), first, R,
+                                                           L, nt, kmax, reverse, stop_on_fail);
+  else if (E == 8)
+    push_rounds_cursor<unsigned long long><<<blocks, block, 0, st>>>(
+        v, counts, static_cast<const unsigned long long*>(vals), first, R, L, nt, kmax, reverse, stop_on_fail);
+  else
+    push_rounds_cursor<uint4><<<blocks, block, 0, st>>>(v, counts, static_cast<const uint4*>(vals), first, R, L, nt,
+                                                        kmax, reverse, stop_on_fail);
+  return launched();
+}
+
+int user_push_formula(const void* view, const uint32_t* counts, uint32_t R, uint32_t L, uint32_t NT, int cursor,
+                      void* stream) {
+  push_formula<<<L, NT, 0, static_cast<cudaStream_t>(stream)>>>(static_cast<const gga_dev_view*>(view), counts, R, L,
+                                                                 NT, cursor);
   return launched();
 }
 

@@ -57,23 +57,26 @@ def expected_first(counts, size0):
     return before[..., None] + np.cumsum(c, axis=2) - c
 
 
-def push(user, g, counts, vals, bx, by, kmax, blocks=None, reverse=0, stop_on_fail=1):
+def push(user, g, counts, vals, bx, by, kmax, blocks=None, reverse=0, stop_on_fail=1, cursor=False):
+    """The rounds through block_push_back calls, or (cursor) a BlockPusher."""
     R, L, NT = counts.shape
     assert bx * by == NT and vals.shape[0] == R * L * NT * kmax
     cd = counts_to_dev(counts)
     vd = values_to_dev(vals, g.E)
     first = torch.empty(R * L * NT, dtype=torch.int64, device="cuda")
-    rc = user.user_push_rounds(ctypes.c_void_p(g.device_view()), ctypes.c_void_p(cd.data_ptr()),
-                               ctypes.c_void_p(vd.data_ptr()), ctypes.c_void_p(first.data_ptr()), R, L, bx, by,
-                               kmax, g.E, blocks or L, reverse, stop_on_fail, stream_ptr())
+    fn = user.user_push_rounds_cursor if cursor else user.user_push_rounds
+    rc = fn(ctypes.c_void_p(g.device_view()), ctypes.c_void_p(cd.data_ptr()), ctypes.c_void_p(vd.data_ptr()),
+            ctypes.c_void_p(first.data_ptr()), R, L, bx, by, kmax, g.E, blocks or L, reverse, stop_on_fail,
+            stream_ptr())
     assert rc == 0
     g.device_commit()
     return first.cpu().numpy().view(np.uint64).reshape(R, L, NT)
 
 
+@pytest.mark.parametrize("cursor", [False, True])
 @pytest.mark.parametrize("E", [4, 8, 16])
-@pytest.mark.parametrize("bx,by", [(128, 1), (100, 1), (16, 6), (1, 1), (1024, 1), (8, 4)])
-def test_user_kernel_pushes_match_oracle(user, E, bx, by):
+@pytest.mark.parametrize("bx,by", [(128, 1), (100, 1), (16, 6), (1, 1), (1024, 1), (8, 4), (33, 31)])
+def test_user_kernel_pushes_match_oracle(user, E, bx, by, cursor):
     rng = np.random.default_rng(100 * E + bx + by)
     L, B, kmax = 7, 8, 3
     NT = bx * by
@@ -81,7 +84,7 @@ def test_user_kernel_pushes_match_oracle(user, E, bx, by):
     for step, R in enumerate((9, 1, 4)):
         size0 = o.sizes().astype(np.int64)
         counts, vals, packed = padded_rounds(rng, R, L, NT, kmax, E, seed=1000 * step + E)
-        first = push(user, g, counts, vals, bx, by, kmax)
+        first = push(user, g, counts, vals, bx, by, kmax, cursor=cursor)
         o.insert(counts, packed)
         assert g.last_error() == gga.GGA_OK
         assert_same_state(g, o)
@@ -108,18 +111,23 @@ def test_device_pushes_and_library_insertions_interleave(user):
     counts, vals, packed = padded_rounds(rng, 3, L, T, kmax, E, seed=4)
     push(user, g, counts, vals, 32, 3, kmax)
     o.insert(counts, packed)
+    counts, vals, packed = padded_rounds(rng, 5, L, T, kmax, E, seed=5)
+    push(user, g, counts, vals, 96, 1, kmax, cursor=True)
+    o.insert(counts, packed)
     assert g.last_error() == gga.GGA_OK
     assert_same_state(g, o)
     g.close()
 
 
-def test_grid_stride_blocks_and_reversed_lfvectors(user):
-    # Fewer blocks than LFVectors, each block serving several in reverse.
+@pytest.mark.parametrize("cursor", [False, True])
+def test_grid_stride_blocks_and_reversed_lfvectors(user, cursor):
+    # Fewer blocks than LFVectors, each block serving several in reverse
+    # (with cursors: one after another on the same shared slots).
     rng = np.random.default_rng(6)
     L, T, B, E, kmax = 50, 64, 4, 8, 4
     g, o = make_pair(L, T, B, E, pool_bytes=64 << 20)
     counts, vals, packed = padded_rounds(rng, 5, L, T, kmax, E, seed=6)
-    first = push(user, g, counts, vals, T, 1, kmax, blocks=7, reverse=1)
+    first = push(user, g, counts, vals, T, 1, kmax, blocks=7, reverse=1, cursor=cursor)
     o.insert(counts, packed)
     assert g.last_error() == gga.GGA_OK
     assert_same_state(g, o)
@@ -207,8 +215,9 @@ def round_chunks(counts, packed, l):
     return [packed[start[r * L + l]:start[r * L + l + 1]] for r in range(R)]
 
 
+@pytest.mark.parametrize("cursor", [False, True])
 @pytest.mark.parametrize("stop_on_fail", [1, 0])
-def test_pool_exhaustion_keeps_whole_rounds(user, stop_on_fail):
+def test_pool_exhaustion_keeps_whole_rounds(user, stop_on_fail, cursor):
     # A pool too small for every LFVector: a block whose buckets do not fit
     # pushes nothing that round and latches POOL_EXHAUSTED; each LFVector holds
     # whole rounds in order (a prefix of them when the kernel stops there).
@@ -216,7 +225,7 @@ def test_pool_exhaustion_keeps_whole_rounds(user, stop_on_fail):
     L, T, B, E, kmax = 16, 64, 16, 4, 3
     g = gga.GGArray(L, T, B, E, 96 << 10)
     counts, vals, packed = padded_rounds(rng, 12, L, T, kmax, E, seed=11)
-    push(user, g, counts, vals, T, 1, kmax, stop_on_fail=stop_on_fail)
+    push(user, g, counts, vals, T, 1, kmax, stop_on_fail=stop_on_fail, cursor=cursor)
     n, rc, sizes, caps = g.sizes_caps()
     assert rc == gga.GGA_ERR_POOL_EXHAUSTED
     sizes, caps = sizes.cpu().numpy(), caps.cpu().numpy()
@@ -344,3 +353,35 @@ def test_push_generated_pool_exhaustion_keeps_whole_leading_rounds():
         short += int(sizes[l]) < kept[-1]
     assert short > 0
     g.close()
+
+
+@pytest.mark.parametrize("cursor", [False, True])
+def test_counts_too_large_for_32_bit_scans(user, cursor):
+    # One thread pushes 2^26 + 3 elements in a round (its warp's and the
+    # block's sums need 64-bit scans), crossing many buckets in its own run;
+    # the other threads push a few.  Values are a formula of (r, l, t, k).
+    L, T, B, E, R = 2, 64, 1024, 8, 2
+    counts = np.zeros((R, L, T), dtype=np.uint32)
+    counts[0, 0, 5] = (1 << 26) + 3
+    counts[0, 0, 40] = 7
+    counts[0, 1, :] = 1
+    counts[1, 0, :] = 2
+    counts[1, 1, 63] = 1 << 20
+    rr, ll, tt = np.nonzero(counts >= 0)
+    c = counts.reshape(-1).astype(np.int64)
+    starts = np.repeat(np.cumsum(c) - c, c)
+    k = np.arange(int(c.sum()), dtype=np.int64) - starts
+    head = ((rr.astype(np.uint64) << np.uint64(56)) | (ll.astype(np.uint64) << np.uint64(48))
+            | (tt.astype(np.uint64) << np.uint64(32)))
+    packed = np.repeat(head, c) | k.astype(np.uint64)
+    g = gga.GGArray(L, T, B, E, 3 << 30)
+    o = oracle.OracleGGArray(L, T, B, E)
+    cd = counts_to_dev(counts)
+    assert user.user_push_formula(ctypes.c_void_p(g.device_view()), ctypes.c_void_p(cd.data_ptr()), R, L, T,
+                                  1 if cursor else 0, stream_ptr()) == 0
+    g.device_commit()
+    o.insert(counts, packed)
+    assert g.last_error() == gga.GGA_OK
+    assert_same_state(g, o)
+    g.close()
+    o.close()

@@ -37,7 +37,9 @@ def load_user() -> ctypes.CDLL:
     vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
     sig = {
         "user_push_rounds": [vp, vp, vp, vp, u32, u32, u32, u32, u32, u32, u32, i32, i32, vp],
+        "user_push_rounds_cursor": [vp, vp, vp, vp, u32, u32, u32, u32, u32, u32, u32, i32, i32, vp],
         "user_push_own": [vp, vp, vp, u32, u32, u32, vp],
+        "user_push_formula": [vp, vp, u32, u32, u32, i32, vp],
         "user_read_global": [vp, vp, u64, vp, vp, u32, vp],
         "user_read_local": [vp, vp, vp, u64, vp, vp, u32, vp],
         "user_push_rejected": [vp, i32, vp, vp],
