@@ -74,7 +74,7 @@ def parse_args():
 # Source files that define each kernel: a recorded DRAM traffic figure is
 # only used while their hash matches the one stored with it.
 SECTOR_BYTES = 32   # DRAM/L2 sector: the least a random element access moves
-DEVICE_H = "include/gga_device.cuh"
+DEVICE_H = "include/gga_layout.cuh"
 KERNEL_SOURCES = {
     "write_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
     "read_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],

@@ -1,17 +1,18 @@
 // gga_core.cuh -- device-side building blocks of the library's kernels.
 //
 // The array's layout in HBM, the device pool, the bucket index math, the
-// prefix-sum search and bucket allocation are in gga_device.cuh (the
-// public device API, also used by user kernels); this file adds what only
-// the library's kernels use: retry and spin bounds, pool queue pushes and
-// fix-up, the mbarrier / bulk-copy PTX wrappers and the launchers.
+// prefix-sum search and bucket allocation are in the public header
+// gga_layout.cuh (shared with the device API that user kernels include);
+// this file adds what only the library's kernels use: retry and spin
+// bounds, pool queue pushes and fix-up, the mbarrier / bulk-copy PTX
+// wrappers and the launchers.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "gga.h"
-#include "gga_device.cuh"
+#include "gga_layout.cuh"
 
 namespace gga {
 
@@ -40,7 +41,7 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 }
 
 // ---------------------------------------------------------------------------
-// Device pool queue operations (the pops are in gga_device.cuh).
+// Device pool queue operations (the pops are in gga_layout.cuh).
 
 // Queue a bucket of byte class c (clear kernels only).  Returns false if the
 // pool does not serve the class.

@@ -4,6 +4,7 @@
 // paper states it: one block per LFVector, one push per round, through the
 // device API's BlockPusher).
 #include "gga_core.cuh"
+#include "gga_device.cuh"
 #include "gga_gen.cuh"
 
 namespace gga {

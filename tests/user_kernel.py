@@ -13,7 +13,7 @@ from paper_2209_00103_gb300 import build
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "cuda", "user_push_back.cu")
 OUT = os.path.join(HERE, "cuda", "_build", "libgga_user_push.so")
-HEADERS = [os.path.join(build.INCLUDE, "gga_device.cuh"), os.path.join(build.INCLUDE, "gga.h")]
+HEADERS = [os.path.join(build.INCLUDE, f) for f in ("gga_device.cuh", "gga_layout.cuh", "gga.h")]
 
 
 def build_user() -> str:
