@@ -115,9 +115,11 @@ def encode_values(v: np.ndarray, E: int) -> np.ndarray:
 class InsertSpec:
     """One batch of R insertion rounds of a GGArray of L blocks x T threads.
 
-    Thread t of block l (gtid = l*T + t) draws its count for round r from
-    ``splitmix_at(seed, (r << 32) | gtid)`` and inserts values
-    ``va*gtid + vb*r + vc*k`` for k < count.
+    Thread t of block l (gtid = gtid0 + l*T + t) draws its count for round r
+    from ``splitmix_at(seed, (r << 32) | gtid)`` and inserts values
+    ``va*gtid + vb*r + vc*k`` for k < count.  gtid0 = l0*T gives the inputs
+    of blocks l0, l0+1, ... of a larger array exactly as that array's own
+    spec would draw them.
     """
     L: int
     T: int
@@ -128,11 +130,12 @@ class InsertSpec:
     round0: int = 0
     coeffs: tuple = (1, 0, 0)
     thresholds: np.ndarray | None = field(default=None, repr=False)
+    gtid0: int = 0
 
     def counts(self) -> np.ndarray:
         """uint32 counts, shape [R][L][T]."""
         r = np.arange(self.round0, self.round0 + self.rounds, dtype=np.uint64)
-        gtid = np.arange(self.L * self.T, dtype=np.uint64)
+        gtid = np.uint64(self.gtid0) + np.arange(self.L * self.T, dtype=np.uint64)
         keys = (r[:, None] << np.uint64(32)) | gtid[None, :]
         h = splitmix_at(self.seed, keys)
         c = draw_counts(self.dist, h, self.thresholds)
@@ -143,7 +146,7 @@ class InsertSpec:
         R = counts.shape[0]
         flat = counts.reshape(-1).astype(np.int64)
         n = int(flat.sum())
-        gtid = np.tile(np.arange(self.L * self.T, dtype=np.uint64), R)
+        gtid = np.tile(np.uint64(self.gtid0) + np.arange(self.L * self.T, dtype=np.uint64), R)
         rnd = np.repeat(np.arange(self.round0, self.round0 + R, dtype=np.uint64), self.L * self.T)
         g_rep = np.repeat(gtid, flat)
         r_rep = np.repeat(rnd, flat)

@@ -34,3 +34,16 @@ def test_indices_numpy_torch_agree():
         va = wl.index_keyed_values(4, a, E)
         vb = wl.index_keyed_values_t(4, torch.from_numpy(a.view(np.int64)), E)
         assert va.tobytes() == vb.contiguous().numpy().tobytes()
+
+
+def test_gtid0_gives_one_blocks_inputs_of_a_larger_spec():
+    # The inputs of block 4 of a 6-block spec, drawn on their own with
+    # gtid0 = 4*T: the same counts and the same values, in the same order.
+    kw = dict(T=32, E=4, seed=3, dist="uniform3", rounds=5, coeffs=(3, 1 << 20, 1 << 9))
+    c, v = wl.InsertSpec(L=6, **kw).make()
+    cp, vp = wl.InsertSpec(L=1, gtid0=4 * 32, **kw).make()
+    assert np.array_equal(cp[:, 0, :], c[:, 4, :])
+    flat = c.reshape(-1).astype(np.int64)
+    starts = np.cumsum(flat) - flat
+    sel = [v[int(starts[(r * 6 + 4) * 32]):int(starts[(r * 6 + 4) * 32]) + int(c[r, 4].sum())] for r in range(5)]
+    assert np.array_equal(np.concatenate(sel), vp)
