@@ -64,6 +64,7 @@ def parse_args():
                          "served: continuous-batching request server")
     ap.add_argument("--duration", type=float, default=10.0, help="served: seconds of offered load")
     ap.add_argument("--newborn", action="store_true", help="two_phase: only the previous generation spawns")
+    ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays (a smaller case for profiling)")
     ap.add_argument("--n0", type=int, default=1 << 24, help="two_phase: initial records (a smaller case for profiling)")
     ap.add_argument("--generations", type=int, default=8, help="two_phase: spawning generations")
     ap.add_argument("--deadline", type=float, default=None,
@@ -707,7 +708,7 @@ def run_batched(args, world, rank, local):
     from paper_2209_00103_gb300 import batching
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    sizes = batching.batched_sizes()
+    sizes = batching.batched_sizes(args.arrays)
     rule = batching.tuned_rule()
     pool, arrays, batch, params = batching.build(sizes, rule, stream)
     total = int(sizes.sum())
@@ -734,11 +735,11 @@ def run_batched(args, world, rank, local):
     plain_ms = batching.plain_time(arrays, sizes, stream)
     peak, _ = peaks()
     gbs = bytes_written / (ms / 1e3) / 1e9
-    res = {"metric": "batched GGArray growth Gelem/s (4096 arrays, one persistent launch)", "value": round(value, 3),
+    res = {"metric": f"batched GGArray growth Gelem/s ({len(sizes)} arrays, one persistent launch)", "value": round(value, 3),
            "unit": "Gelem/s", "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u32/u64/record", "data": "synthetic",
-           "config": {"workload": "batched_4096_lognormal_median64K_sigma1.5_cap16M", "arrays": len(sizes),
+           "config": {"workload": f"batched_{len(sizes)}_lognormal_median64K_sigma1.5_cap16M", "arrays": len(sizes),
                       "elements": total, "bytes": bytes_written, "rule": rule.__dict__,
                       "step": "captured graph: clear every array + one persistent grow launch + fix-up + finalize"},
            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",

@@ -49,7 +49,7 @@ __device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* s
   // Rounds per pass: a pass of T <= 1024 threads at one element per thread
   // and round then averages <= 32 KB, inside the 48 KB stage.
   constexpr int K = E == 4 ? 8 : (E == 8 ? 4 : 2);
-  const uint32_t drawn = grow_passes<E, K, 2>(v, J.g, l, kBatchMaxRounds, target, sh, stage, kBatchStageBytes / E);
+  const uint32_t drawn = grow_passes<E, K, 2, true>(v, J.g, l, kBatchMaxRounds, target, sh, stage, kBatchStageBytes / E);
   if (threadIdx.x == 0 && sh.stop == 0 && drawn >= kBatchMaxRounds) latch_error(v.status, GGA_ERR_TIMEOUT);
   __syncthreads();
 }
@@ -60,14 +60,22 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_grow_kernel(const Batc
   extern __shared__ uint4 s_stage4[];
   __shared__ GenShared sh;
   __shared__ uint32_t s_item;
+  // The item's job (its view and draws) in shared memory: the pass loop
+  // reads these fields over and over, and from here they are shared-memory
+  // loads instead of global ones.
+  __shared__ __align__(16) BatchJob s_job;
+  static_assert(sizeof(BatchJob) % 8 == 0, "job copied in 8-byte words");
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t it = s_item;
-    __syncthreads();
     if (it >= n_items) break;
     const BatchItem item = items[it];
-    const BatchJob& J = jobs[item.job];
+    if (threadIdx.x < sizeof(BatchJob) / 8)
+      reinterpret_cast<unsigned long long*>(&s_job)[threadIdx.x] =
+          reinterpret_cast<const unsigned long long*>(jobs + item.job)[threadIdx.x];
+    __syncthreads();
+    const BatchJob& J = s_job;
     switch (J.v.E) {
       case 4: grow_item<4>(J, item.l, sh, s_stage4); break;
       case 8: grow_item<8>(J, item.l, sh, s_stage4); break;

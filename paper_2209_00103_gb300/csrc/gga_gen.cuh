@@ -3,13 +3,16 @@
 // finalize (prefix sum of LFVector sizes, Sec. IV; work lists).
 #pragma once
 
+#include <type_traits>
+
 #include "gga_core.cuh"
 
 namespace gga {
 
 struct GenParams {
   uint64_t seed, va, vb, vc;
-  uint32_t dist, nthr, round0, pad;
+  uint32_t dist, nthr, round0;
+  uint32_t thr_sorted;   // 1: thr[0..nthr) ascending (set on the host)
   uint32_t thr[GGA_MAX_THRESHOLDS];
 };
 
@@ -22,6 +25,11 @@ __device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t key) {
   return z ^ (z >> 31);
 }
 
+// SEARCH: g lives in shared memory, where a binary search over the
+// thresholds costs a few indexed loads; for kernel parameters (constant
+// bank) the unrolled count reads each threshold as an operand instead, and
+// an indexed read would copy the parameters to local memory.
+template <bool SEARCH = false>
 __device__ __forceinline__ uint32_t gen_count(const GenParams& g, uint64_t h) {
   switch (g.dist) {
     case GGA_DIST_BERNOULLI:
@@ -33,10 +41,19 @@ __device__ __forceinline__ uint32_t gen_count(const GenParams& g, uint64_t h) {
       return inv == 0 ? 63u : min(63u, static_cast<uint32_t>(__ffsll(static_cast<long long>(inv)) - 1));
     }
     default: {
+      // c = #{k < nthr : u >= thr[k]}.  Ascending thresholds (the CDF of the
+      // distribution, the usual case) make that set a prefix, whose length
+      // a binary search finds in five steps; other tables are counted.
       const uint32_t u = static_cast<uint32_t>(h >> 32);
       uint32_t c = 0;
+      if (SEARCH && g.thr_sorted) {
 #pragma unroll
-      for (uint32_t k = 0; k < GGA_MAX_THRESHOLDS; ++k) c += (k < g.nthr) & (u >= g.thr[k]);
+        for (uint32_t step = 16; step > 0; step >>= 1)
+          if (c + step <= g.nthr && u >= g.thr[c + step - 1]) c += step;
+      } else {
+#pragma unroll
+        for (uint32_t k = 0; k < GGA_MAX_THRESHOLDS; ++k) c += (k < g.nthr) & (u >= g.thr[k]);
+      }
       return c;
     }
   }
@@ -65,8 +82,10 @@ inline GenParams make_gen_params(const gga_gen_spec& spec) {
   g.dist = spec.dist;
   g.nthr = spec.n_thresholds;
   g.round0 = spec.round0;
-  g.pad = 0;
+  g.thr_sorted = 1;
   for (int i = 0; i < GGA_MAX_THRESHOLDS; ++i) g.thr[i] = spec.thresholds[i];
+  for (uint32_t i = 1; i < spec.n_thresholds && i < GGA_MAX_THRESHOLDS; ++i)
+    if (g.thr[i] < g.thr[i - 1]) g.thr_sorted = 0;
   return g;
 }
 
@@ -170,7 +189,8 @@ __device__ __forceinline__ void put_gen_elem(uint64_t addr, typename Elem<E>::T 
 }
 
 // Returns the number of rounds it drew.  Every thread of the block calls it.
-template <int E, int K, int KV>
+// SEARCH as for gen_count (g in shared memory).
+template <int E, int K, int KV, bool SEARCH = false>
 __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t l, uint32_t R, uint64_t target,
                                 GenShared& sh, uint4* stage4, uint32_t cap) {
   typedef typename Elem<E>::T T;
@@ -204,8 +224,9 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
         uint32_t c0 = 0, c1 = 0;
         if (k < kk) {
-          if (tfirst < v.T) c0 = gen_count(g, splitmix(g.seed, (r << 32) | gfirst));
-          if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = gen_count(g, splitmix(g.seed, (r << 32) | (gfirst + 1)));
+          if (tfirst < v.T) c0 = gen_count<SEARCH>(g, splitmix(g.seed, (r << 32) | gfirst));
+          if (KV > 1 && kv > 1 && tfirst + 1 < v.T)
+            c1 = gen_count<SEARCH>(g, splitmix(g.seed, (r << 32) | (gfirst + 1)));
         }
         cc[k] = c0 | (c1 << 8);
         c[h] = c0 + c1;
@@ -274,8 +295,12 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         for (int i = 0; i < KV; ++i) {
           const uint32_t c = (cc[k] >> (8 * i)) & 0xFFu;
           if (c == 0) continue;
-          uint64_t val = g.va * (gfirst + i) + g.vb * (static_cast<uint64_t>(g.round0) + r0 + k);
-          for (uint32_t m = 0; m < c; ++m, val += g.vc) {
+          // A 4-byte element keeps the low 32 bits of the value, which
+          // 32-bit arithmetic gives exactly.
+          typedef typename std::conditional<E == 4, uint32_t, uint64_t>::type V;
+          V val = static_cast<V>(g.va) * static_cast<V>(gfirst + i) +
+                  static_cast<V>(g.vb) * static_cast<V>(static_cast<uint64_t>(g.round0) + r0 + k);
+          for (uint32_t m = 0; m < c; ++m, val += static_cast<V>(g.vc)) {
             const uint32_t q = st + m;
             if (q >= commit) break;
             if (staged) {
