@@ -30,7 +30,8 @@ def lfv_oracle(l):
 
 def test_generated_array_beyond_2_32_elements():
     free, _ = torch.cuda.mem_get_info()
-    assert free > (64 << 30), "needs ~55 GB of device memory"
+    if free < (64 << 30):
+        pytest.skip(f"needs ~55 GB of free device memory, {free >> 30} GB free")
     g = gga.GGArray(L, T, B, E, 36 << 30)
     g.insert_generated(gga.make_gen_spec(SEED, DIST, COEFFS), R)
     n, rc, sizes, caps = g.sizes_caps()
