@@ -385,3 +385,37 @@ def test_counts_too_large_for_32_bit_scans(user, cursor):
     assert_same_state(g, o)
     g.close()
     o.close()
+
+
+def test_pushes_into_arrays_of_one_shared_pool_reuse_cleared_buckets(user):
+    # Two arrays of one pool pushed from user kernels; A is cleared (its
+    # buckets go to the pool's queues) and B's next pushes take them.  The
+    # commits fold the queue pops; both arrays match their oracles, and the
+    # pool hands out no new slab bytes for B's second growth while A's
+    # queued buckets cover it.
+    rng = np.random.default_rng(13)
+    T, B, E, kmax = 64, 16, 4, 3
+    pool = gga.GGAPool(64 << 20, B * E)
+    a = gga.GGArray(10, T, B, E, shared_pool=pool)
+    b = gga.GGArray(10, T, B, E, shared_pool=pool)
+    oa, ob = oracle.OracleGGArray(10, T, B, E), oracle.OracleGGArray(10, T, B, E)
+    ca, va, pa = padded_rounds(rng, 6, 10, T, kmax, E, seed=30)
+    cb, vb, pb = padded_rounds(rng, 2, 10, T, kmax, E, seed=31)
+    push(user, a, ca, va, T, 1, kmax, cursor=True)
+    oa.insert(ca, pa)
+    push(user, b, cb, vb, T, 1, kmax)
+    ob.insert(cb, pb)
+    assert_same_state(a, oa)
+    assert_same_state(b, ob)
+    bump_before = pool.info()["bump_bytes"]
+    a.clear()
+    oa.close()
+    cb2, vb2, pb2 = padded_rounds(rng, 4, 10, T, kmax, E, seed=32)
+    push(user, b, cb2, vb2, T, 1, kmax, cursor=True)
+    ob.insert(cb2, pb2)
+    assert b.last_error() == gga.GGA_OK
+    assert_same_state(b, ob)
+    assert pool.info()["bump_bytes"] == bump_before
+    b.close()
+    a.close()
+    pool.close()
