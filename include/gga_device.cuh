@@ -25,6 +25,10 @@
 // (two when the push reaches new buckets), against two for each
 // block_push_back call.
 //
+// A kernel launched with blocks of up to 1024 threads should say so
+// (__launch_bounds__(1024)) so that the compiler keeps it within the
+// register file.
+//
 // Rules (the paper's phase separation, Sec. VI):
 //  - every thread of the block calls block_push_back with the same
 //    LFVector l (it holds two block barriers); l < L;

@@ -15,7 +15,7 @@ namespace {
 // LFVector-local index in first[r][l][t].  Threads are laid out in 2-D when
 // blockDim.y > 1 (rank = x + blockDim.x * y).
 template <class T>
-__global__ void push_rounds(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint64_t* first, uint32_t R,
+__global__ void __launch_bounds__(1024) push_rounds(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint64_t* first, uint32_t R,
                             uint32_t L, uint32_t NT, uint32_t kmax, int reverse, int stop_on_fail) {
   const uint32_t t = gga::block_rank();
   for (uint32_t i = blockIdx.x; i < L; i += gridDim.x) {
@@ -35,7 +35,7 @@ __global__ void push_rounds(const gga_dev_view* v, const uint32_t* counts, const
 // The same rounds through a BlockPusher per LFVector (one shared slot set,
 // reused by the block's successive cursors).
 template <class T>
-__global__ void push_rounds_cursor(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint64_t* first,
+__global__ void __launch_bounds__(1024) push_rounds_cursor(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint64_t* first,
                                    uint32_t R, uint32_t L, uint32_t NT, uint32_t kmax, int reverse, int stop_on_fail) {
   __shared__ gga::PushShared sh;
   const uint32_t t = gga::block_rank();
@@ -57,7 +57,7 @@ __global__ void push_rounds_cursor(const gga_dev_view* v, const uint32_t* counts
 // Rounds whose values are a formula of (round, LFVector, thread, k), for
 // counts too large to hold their values in an array: element k of thread t
 // of LFVector l in round r is (r << 56) | (l << 48) | (t << 32) | k.
-__global__ void push_formula(const gga_dev_view* v, const uint32_t* counts, uint32_t R, uint32_t L, uint32_t NT,
+__global__ void __launch_bounds__(1024) push_formula(const gga_dev_view* v, const uint32_t* counts, uint32_t R, uint32_t L, uint32_t NT,
                              int cursor) {
   __shared__ gga::PushShared sh;
   const uint32_t t = gga::block_rank();
@@ -79,7 +79,7 @@ __global__ void push_formula(const gga_dev_view* v, const uint32_t* counts, uint
 
 // One LFVector per block, the short form (l = blockIdx.x), one round.
 template <class T>
-__global__ void push_own(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint32_t kmax) {
+__global__ void __launch_bounds__(1024) push_own(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint32_t kmax) {
   const uint32_t t = gga::block_rank();
   const uint64_t row = static_cast<uint64_t>(blockIdx.x) * gga::block_threads() + t;
   const T* mine = vals + row * kmax;
