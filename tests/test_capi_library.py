@@ -44,3 +44,16 @@ def test_binding_names_match_header():
     from paper_2209_00103_gb300 import gga
     assert sorted(gga.EXPORTED) == declared_symbols()
 
+
+
+@pytest.mark.parametrize("header", sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")))
+def test_headers_compile_alone_as_c_and_cpp(header, tmp_path):
+    # The C ABI's headers are usable from plain C (C99) and from C++ with
+    # nothing else included first.
+    src = tmp_path / "t.c"
+    src.write_text(f'#include "{header}"\nint main(void) {{ return 0; }}\n')
+    inc = "-I" + os.path.join(ROOT, "include")
+    for cmd in (["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", inc, "-fsyntax-only", str(src)],
+                ["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", inc, "-x", "c++", "-fsyntax-only", str(src)]):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
