@@ -68,6 +68,34 @@ def test_small_batch_matches_oracle():
     pool.close()
 
 
+@pytest.mark.parametrize("order", ["ascending", "shuffled"])
+def test_threshold_tables_in_any_order(order):
+    # A Poisson-style count is #{k : u >= thr[k]}.  The batch kernel finds
+    # it by binary search when the table is ascending and counts it
+    # otherwise; both must give the oracle's counts.  The shuffled table
+    # also carries thresholds equal to each other and to 0 and 2^32 - 1.
+    thr = np.array(list(wl.poisson1_thresholds()) + [0, 0xFFFFFFFF, 1 << 31], dtype=np.uint32)
+    thr = np.sort(thr) if order == "ascending" else np.random.default_rng(5).permutation(thr)
+    pool = gga.GGAPool(128 << 20, 256 * 4)
+    jobs, refs = [], []
+    for a, (T, E, target) in enumerate([(512, 4, 70000), (1024, 8, 30001), (100, 16, 9999), (32, 4, 5)]):
+        spec = gga.make_gen_spec(40 + a, "poisson", (3, 1 << 20, 1), thresholds=thr)
+        g = gga.GGArray(3, T, 256, E, shared_pool=pool)
+        o = oracle.OracleGGArray(3, T, 256, E)
+        o.grow_to_target(40 + a, "poisson", (3, 1 << 20, 1), target, thresholds=thr)
+        jobs.append((g, spec, target))
+        refs.append(o)
+    batch = gga.GGABatch(jobs)
+    batch.grow()
+    for (g, _, target), o in zip(jobs, refs):
+        assert_same_state(g, o)
+        assert g.size()[0] == target
+    batch.close()
+    for g, _, _ in jobs:
+        g.close()
+    pool.close()
+
+
 def test_batched_workload_4096_arrays():
     sizes = batching.batched_sizes()
     assert len(sizes) == 4096 and sizes.max() <= (16 << 20) and sizes.min() >= 1
