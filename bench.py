@@ -56,7 +56,8 @@ def parse_args():
     ap.add_argument("--no-baselines", action="store_true", help="skip the static / semi-static flat arrays")
     ap.add_argument("--nvtx", action="store_true", help="NVTX range around every phase of a step (for a profiler)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="steps of the end-to-end loop (default: --steps, as the device-timed loop)")
     ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling",
                                            "insertion", "phases"],
                     default="paper_growth",
@@ -230,7 +231,11 @@ class ClockSampler:
 # The GPU arm.
 
 def algorithmic_bytes(N, R, L, T, E, n_rand):
-    """Bytes each phase must move at minimum (see the design notes)."""
+    """Bytes each phase must move at minimum: insertion reads the R*L*T
+    4-byte counts and the N packed values and writes the N elements; a
+    random read or write moves its 8-byte index, the element and the
+    output (or input) value; sweeps and flatten read and write every
+    element once."""
     counts = R * L * T * 4
     return {
         "insert": counts + 2 * N * E,          # counts read, values read, elements written
@@ -578,7 +583,7 @@ def run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world,
         step(k)
     torch.cuda.synchronize(dev)
     barrier(world)
-    K = args.e2e_steps
+    K = args.e2e_steps if args.e2e_steps is not None else args.steps
     a = torch.cuda.Event(enable_timing=True)
     b_ev = torch.cuda.Event(enable_timing=True)
     a.record(stream)

@@ -181,14 +181,21 @@ int gga_insert(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
  *  round's position in each LFVector's batch) in a buffer it grows on
  *  demand.  This variant instead uses one fixed 32 MiB array compiled into
  *  the library as a static __device__ variable, so it calls no cudaMalloc,
- *  cudaFree or allocating library routine.  Every GPU that loads the
- *  library holds those 32 MiB until the process exits.  A call needs at
+ *  cudaFree or allocating library routine.  Every GPU on which a handle
+ *  was created holds those 32 MiB until the process exits.  A call needs at
  *  most about 16.5 * rounds * L bytes of it (rounds * L <= ~2 million, e.g.
  *  512 rounds of 1024 LFVectors use 8.5 MiB); a call that needs more
  *  returns GGA_ERR_TOO_LARGE and enqueues nothing.
- *  Set-up: the first call on a device looks the array up there
- *  (cudaGetSymbolAddress, with that device current); make that first call
- *  before any stream capture.  The current device must be the handle's.
+ *  Set-up: the array's device address is looked up once per device
+ *  (cudaGetSymbolAddress, with that device current).  gga_create and
+ *  gga_create_in_pool do that lookup on the handle's device, which is also
+ *  when the library's module holding the array is loaded there and its
+ *  32 MiB are committed (CUDA loads modules lazily by default): create the
+ *  handles before reserving the rest of the device.  If that lookup failed
+ *  at creation, the first call on the device makes it again (make such a
+ *  call before any stream capture) and returns GGA_ERR_CUDA if it fails
+ *  again; the runtime's last-error state is left clear either way.  The
+ *  current device must be the handle's.
  *  Sharing: all calls, on all handles, share the one array and it keeps the
  *  last call's contents (a call writes every part of it before reading it).
  *  Calls that overlap on the GPU -- on different streams, or from different

@@ -30,7 +30,7 @@
 //   * The r/w operation of Sec. VI-C: a kernel that adds +1 thirty times to
 //     every element; modelled as "add delta, repeats times".
 //
-// Readings where the paper is silent (also listed in the design notes):
+// Readings where the paper is silent (Sec. IV and Algorithms 1-2 leave these open):
 //   * log in Algorithm 2 is log2 and B must be a power of two;
 //   * buckets are allocated lazily, so an empty LFVector has capacity 0;
 //   * a read/write of a global index >= size is an error;

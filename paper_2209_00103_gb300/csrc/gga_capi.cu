@@ -301,6 +301,9 @@ static int handle_make(const gga_params* p, gga_pool_t* pool, bool own_pool, cud
     gga_destroy(h);
     return rc;
   }
+  // Commit gga_insert_noalloc's fixed scratch on this device now, so that
+  // no call of that entry point is the one that places it.
+  gga::noalloc_prepare(h->device);
   *out = h;
   return GGA_OK;
 }

@@ -215,5 +215,7 @@ ArrayView* handle_dview(gga_handle h);
 PoolState* handle_pool(gga_handle h);
 uint64_t* handle_serve_records(gga_handle h, uint64_t slots);
 uint64_t count_tiles(uint64_t n_rows, uint32_t T, bool vec_ok);
+// Places gga_insert_noalloc's fixed scratch on device `dev` (current).
+void noalloc_prepare(int dev);
 
 }  // namespace gga

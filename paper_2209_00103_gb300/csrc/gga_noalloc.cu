@@ -10,11 +10,14 @@
 // nothing is allocated during the call.  It is an interface variant; the
 // paper has no counterpart.
 //
-// The array lives in device memory of every GPU that loads the library, for
+// The array lives in device memory of every GPU that uses the library, for
 // the life of the process.  Host code cannot use its name as an address (in
 // host code the name denotes a host-side shadow), so the device address is
 // looked up once per device with cudaGetSymbolAddress, with that device
-// current, and passed to the kernels.
+// current, and passed to the kernels.  Under CUDA's lazy module loading the
+// array is placed on a device only when it is first looked up there; handle
+// creation does that lookup (noalloc_prepare), so the 32 MiB are committed
+// while the caller creates its arrays, not inside a gga_insert_noalloc call.
 #include <mutex>
 
 #include "gga_core.cuh"
@@ -32,19 +35,34 @@ void* g_scratch_addr[kMaxDevices] = {};
 inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Device address of the fixed scratch on the current device, looked up on
-// the first call there.  Returns nullptr on failure.
+// the first request there.  Returns nullptr on failure, with the runtime's
+// last-error state cleared so that a later, unrelated launch check does not
+// report this failure.
 void* scratch_on_device(int dev) {
   if (dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (g_scratch_addr[dev] == nullptr) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, gga_noalloc_scratch) != cudaSuccess) return nullptr;
+    if (cudaGetSymbolAddress(&p, gga_noalloc_scratch) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nullptr;
+    }
     g_scratch_addr[dev] = p;
   }
   return g_scratch_addr[dev];
 }
 
 }  // namespace
+
+namespace gga {
+
+// Called by handle creation with the handle's device current: places the
+// fixed scratch on that device now.  A failure here is not an error of the
+// creation (the array itself does not need the scratch); the next
+// gga_insert_noalloc on the device tries again and reports GGA_ERR_CUDA.
+void noalloc_prepare(int dev) { (void)scratch_on_device(dev); }
+
+}  // namespace gga
 
 extern "C" int gga_insert_noalloc(gga_handle h, const uint32_t* counts_dev, uint32_t rounds,
                                   const void* values_dev, uint64_t n_values, void* stream) {
