@@ -397,6 +397,7 @@ def run_ours(args, world, rank, local):
     # rounds batched in passes, and the device API's one push per round.
     gen = time_generated(w, R, pool_bytes, dev, stream)
     push_gen = time_generated(w, R, pool_bytes, dev, stream, per_round=True)
+    push_exp = time_push_expand(spec, w.B, counts, pool_bytes, dev, stream)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gelem/s", "n_gpus": world, "steps": K,
@@ -417,6 +418,7 @@ def run_ours(args, world, rank, local):
         "memory": mem,
         "insert_generated": gen,
         "push_generated": push_gen,
+        "push_expand": push_exp,
         "gpu_launches": K * (sum(LAUNCHES_PER_STEP.values()) - (0 if binned else 3)),
         "clocks": clocks,
         "e2e": e2e,
@@ -634,6 +636,45 @@ def time_generated(w, R, pool_bytes, dev, stream, per_round=False):
             "device_error": rc,
             "kernels": ("push_generated_kernel" if per_round else "gen_insert_kernel") + " + finalize_kernel",
             "algorithmic_bytes": "E per element (values drawn in registers, write only)"}
+
+
+def time_push_expand(spec, B, counts, pool_bytes, dev, stream):
+    """Pushes of values read from device memory through the device API
+    (gga_push_expand: gga::block_push_rounds, 8 rounds per call): the same
+    counts as the step's insertion, and one int32 input per (round, block,
+    thread) that the thread appends `count` times.  Algorithmic bytes: the
+    counts and inputs read (4 + E per thread and round) and E per element
+    written."""
+    from paper_2209_00103_gb300 import gga
+    from paper_2209_00103_gb300 import workloads as wl
+    inputs = wl.expand_inputs_t(spec, dev)
+    g = gga.GGArray(spec.L, spec.T, B, spec.E, pool_bytes)
+    for _ in range(3):
+        g.clear(stream)
+        g.push_expand(counts, inputs, stream)
+    torch.cuda.synchronize(dev)
+    n, rc = g.size(stream)
+    K = 10
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for a, b in evs:
+        g.clear(stream)
+        a.record(stream)
+        g.push_expand(counts, inputs, stream)
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = statistics.median(a.elapsed_time(b) for a, b in evs)
+    g.close()
+    del inputs
+    slots = counts.numel()
+    alg = slots * (4 + spec.E) + n * spec.E
+    gbs = alg / (ms / 1e3) / 1e9
+    peak, _ = peaks()
+    return {"elements": n, "ms": round(ms, 4), "gelem_s": round(n / (ms / 1e3) / 1e9, 2),
+            "algorithmic_bytes": int(alg), "achieved_gbs": round(gbs, 1), "frac_of_measured_peak": round(gbs / peak, 3),
+            "frac_of_8tbs": round(gbs / 8000.0, 3), "device_error": rc,
+            "kernels": "push_expand_kernel + finalize_kernel",
+            "note": "counts [R][L][T] and one input per (round, block, thread) read from HBM; "
+                    "block_push_rounds of 8 rounds, staged 128-bit stores"}
 
 
 # ---------------------------------------------------------------------------

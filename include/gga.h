@@ -247,11 +247,29 @@ int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds
  *  the device API: one block of T threads per LFVector, one push per round
  *  through a gga::BlockPusher, then gga_device_commit.  Same draws, same
  *  result, same errors as gga_insert_generated; it is the per-round form of
- *  Algorithm 1, which gga_insert_generated batches over rounds.
+ *  Algorithm 1, which gga_insert_generated batches over rounds.  Each push
+ *  is assembled in shared memory and written with 128-bit stores.
+ *
+ * gga_push_expand -- pushes of values read from device memory, written as a
+ *  user kernel of the device API (one block of T <= 512 threads per
+ *  LFVector; gga::block_push_rounds, 8 rounds per call for 4-byte
+ *  elements, 4 for 8-byte, 2 for 16-byte), then gga_device_commit.  In
+ *  round r, thread t of block l appends counts_dev[r][l][t] copies of
+ *  inputs_dev[r][l][t].  counts_dev: device, uint32 [rounds][L][T], 4-byte
+ *  aligned; inputs_dev: device, E-byte elements [rounds][L][T], E-byte
+ *  aligned; both caller-owned, read on `stream`.  The result equals
+ *  gga_insert with the same counts and values_dev = every input repeated
+ *  its count times, in (round, block, thread) order (Algorithm 1 with the
+ *  positions of Sec. III-B).  GGA_ERR_INVALID on the host for a null
+ *  pointer, misalignment or T > 512; GGA_ERR_POOL_EXHAUSTED latched when a
+ *  call's buckets do not fit (the LFVector keeps the longest prefix of
+ *  whole rounds of that call that fits and stops).
  */
 int gga_device_view(gga_handle h, const void** view_dev);
 int gga_device_commit(gga_handle h, void* stream);
 int gga_push_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds, void* stream);
+int gga_push_expand(gga_handle h, const uint32_t* counts_dev, const void* inputs_dev, uint32_t rounds,
+                    void* stream);
 
 /*
  * gga_read -- out_dev[i] = element at global index idx_dev[i], i < n (rw_g

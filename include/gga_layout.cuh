@@ -140,6 +140,49 @@ __device__ __forceinline__ V warp_incl_scan(V v) {
 }
 
 // ---------------------------------------------------------------------------
+// Staged writes (the write step of Algorithm 1 when a block's run of
+// consecutive LFVector positions has been assembled in shared memory).
+// stage holds positions base - shv .. base + n - 1 of LFVector l, position
+// base + q at stage element q + shv, with shv = base mod (16 / sizeof(T));
+// the whole block calls it after a barrier that follows the stage writes.
+// Every 16-byte group of positions inside the run goes out as one aligned
+// 128-bit store (a group never straddles buckets when B is a multiple of
+// 16 / sizeof(T), and buckets start on 256-byte boundaries); the partial
+// groups at the run's ends go element by element.  The buckets are those
+// of `tab` (the LFVector's bucket table), already allocated.
+
+template <class T>
+__device__ __forceinline__ void stage_to_buckets(const uint64_t* tab, uint32_t log2B, uint64_t B, uint64_t base,
+                                                 uint32_t n, uint32_t shv, const uint4* stage4, uint32_t t,
+                                                 uint32_t nt) {
+  constexpr uint32_t VEC = 16 / sizeof(T);
+  const T* stage = reinterpret_cast<const T*>(stage4);
+  const bool group_ok = B >= VEC;
+  const uint64_t gbeg = base - shv;
+  const uint32_t nvec = (n + shv + VEC - 1) / VEC;
+  for (uint32_t vi = t; vi < nvec; vi += nt) {
+    const uint64_t p = gbeg + static_cast<uint64_t>(vi) * VEC;
+    const uint32_t lo = vi * VEC;   // stage index of position p
+    if (group_ok && lo >= shv && lo + VEC <= n + shv) {
+      uint32_t bb;
+      uint64_t off;
+      bucket_of(p, log2B, bb, off);
+      __stcs(reinterpret_cast<uint4*>(tab[bb] + off * sizeof(T)), stage4[vi]);
+    } else {
+#pragma unroll
+      for (uint32_t e = 0; e < VEC; ++e) {
+        const uint32_t si = lo + e;
+        if (si < shv || si >= n + shv) continue;
+        uint32_t bb;
+        uint64_t off;
+        bucket_of(p + e, log2B, bb, off);
+        *reinterpret_cast<T*>(tab[bb] + off * sizeof(T)) = stage[si];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Device pool operations.
 
 __host__ __device__ __forceinline__ uint64_t alloc_bytes_for(uint64_t bytes) {

@@ -49,8 +49,28 @@ __device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* s
   // Rounds per pass: a pass of T <= 1024 threads at one element per thread
   // and round then averages <= 32 KB, inside the 48 KB stage.
   constexpr int K = E == 4 ? 8 : (E == 8 ? 4 : 2);
-  const uint32_t drawn = grow_passes<E, K, 2, true>(v, J.g, l, kBatchMaxRounds, target, sh, stage, kBatchStageBytes / E);
-  if (threadIdx.x == 0 && sh.stop == 0 && drawn >= kBatchMaxRounds) latch_error(v.status, GGA_ERR_TIMEOUT);
+  uint32_t drawn;
+  bool done;
+  // One dispatch per item on the count distribution, none per draw.
+  switch (J.g.dist) {
+    case GGA_DIST_BERNOULLI:
+      drawn = grow_passes<E, K, 2, true, GGA_DIST_BERNOULLI>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
+                                                             kBatchStageBytes / E, &done);
+      break;
+    case GGA_DIST_UNIFORM3:
+      drawn = grow_passes<E, K, 2, true, GGA_DIST_UNIFORM3>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
+                                                            kBatchStageBytes / E, &done);
+      break;
+    case GGA_DIST_GEOMETRIC:
+      drawn = grow_passes<E, K, 2, true, GGA_DIST_GEOMETRIC>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
+                                                             kBatchStageBytes / E, &done);
+      break;
+    default:
+      drawn = grow_passes<E, K, 2, true, GGA_DIST_POISSON>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
+                                                           kBatchStageBytes / E, &done);
+      break;
+  }
+  if (threadIdx.x == 0 && !done && drawn >= kBatchMaxRounds) latch_error(v.status, GGA_ERR_TIMEOUT);
   __syncthreads();
 }
 

@@ -17,18 +17,81 @@ struct GenParams {
 };
 
 // SplitMix64 (Steele, Lea and Flood, 2014): output number key+1 of the
-// stream seeded with `seed`.
-__device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t key) {
-  uint64_t z = seed + (key + 1) * 0x9E3779B97F4A7C15ull;
+// stream seeded with `seed`.  The generator's state after key+1 steps is
+// seed + (key+1) * GOLDEN (a Weyl sequence); the output is that state
+// passed through the mixing function below.
+constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
 
+// The high 32 bits of splitmix_mix(z): the final xor-shift by 31 changes
+// the high word only by its own top bit, so the last step stays in 32 bits.
+__device__ __forceinline__ uint32_t splitmix_mix_hi(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  const uint32_t h = static_cast<uint32_t>(z >> 32);
+  return h ^ (h >> 31);
+}
+
+__device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t key) {
+  return splitmix_mix(seed + (key + 1) * kGolden);
+}
+
+// The draws of one thread over consecutive rounds, for keys
+// (round << 32) | gid.  Write gid = gh * 2^32 + gl (gl < 2^32); the key's
+// high word is then uint32(round) | gh and its low word gl, so the state is
+//   seed + (gl + 1) * GOLDEN + ((hi_word * GOLDEN) mod 2^32) * 2^32,
+// where only the last term depends on the round: one 32-bit multiply and
+// one 32-bit add into the state's high word per draw, instead of a 64-bit
+// multiply.  Equal to splitmix(seed, (round << 32) | gid) for every gid.
+struct RoundDraws {
+  uint64_t base;   // seed + (gl + 1) * GOLDEN
+  uint32_t gh;     // gid >> 32
+  __device__ __forceinline__ RoundDraws(uint64_t seed, uint64_t gid)
+      : base(seed + ((gid & 0xFFFFFFFFull) + 1ull) * kGolden), gh(static_cast<uint32_t>(gid >> 32)) {}
+  __device__ __forceinline__ uint64_t state(uint64_t round) const {
+    const uint32_t hw = (static_cast<uint32_t>(round) | gh) * static_cast<uint32_t>(kGolden);
+    return base + (static_cast<uint64_t>(hw) << 32);
+  }
+};
+
+// Count of one draw from the mixed state z.  DIST >= 0 fixes the
+// distribution at compile time (GGA_DIST_*), -1 reads g.dist.  Every
+// distribution but the geometric one uses only the high word of the draw.
 // SEARCH: g lives in shared memory, where a binary search over the
 // thresholds costs a few indexed loads; for kernel parameters (constant
 // bank) the unrolled count reads each threshold as an operand instead, and
 // an indexed read would copy the parameters to local memory.
+template <bool SEARCH = false, int DIST = -1>
+__device__ __forceinline__ uint32_t gen_count_state(const GenParams& g, uint64_t z) {
+  const uint32_t dist = DIST >= 0 ? static_cast<uint32_t>(DIST) : g.dist;
+  if (dist == GGA_DIST_GEOMETRIC) {
+    const uint64_t inv = ~splitmix_mix(z);
+    return inv == 0 ? 63u : min(63u, static_cast<uint32_t>(__ffsll(static_cast<long long>(inv)) - 1));
+  }
+  const uint32_t u = splitmix_mix_hi(z);
+  if (dist == GGA_DIST_BERNOULLI) return u >> 31;
+  if (dist == GGA_DIST_UNIFORM3) return __umulhi(u, 3u);
+  // c = #{k < nthr : u >= thr[k]}.  Ascending thresholds (the CDF of the
+  // distribution, the usual case) make that set a prefix, whose length a
+  // binary search finds in five steps; other tables are counted.
+  uint32_t c = 0;
+  if (SEARCH && g.thr_sorted) {
+#pragma unroll
+    for (uint32_t step = 16; step > 0; step >>= 1)
+      if (c + step <= g.nthr && u >= g.thr[c + step - 1]) c += step;
+  } else {
+#pragma unroll
+    for (uint32_t k = 0; k < GGA_MAX_THRESHOLDS; ++k) c += (k < g.nthr) & (u >= g.thr[k]);
+  }
+  return c;
+}
+
+// Count of draw h = splitmix(seed, key) (the whole 64-bit output).
 template <bool SEARCH = false>
 __device__ __forceinline__ uint32_t gen_count(const GenParams& g, uint64_t h) {
   switch (g.dist) {
@@ -41,9 +104,6 @@ __device__ __forceinline__ uint32_t gen_count(const GenParams& g, uint64_t h) {
       return inv == 0 ? 63u : min(63u, static_cast<uint32_t>(__ffsll(static_cast<long long>(inv)) - 1));
     }
     default: {
-      // c = #{k < nthr : u >= thr[k]}.  Ascending thresholds (the CDF of the
-      // distribution, the usual case) make that set a prefix, whose length
-      // a binary search finds in five steps; other tables are counted.
       const uint32_t u = static_cast<uint32_t>(h >> 32);
       uint32_t c = 0;
       if (SEARCH && g.thr_sorted) {
@@ -156,14 +216,17 @@ __device__ inline void finalize_block(const ArrayView& v, const uint64_t* ins_ba
 // Per pass every thread draws its counts for K rounds (virtual threads
 // t = t0 * kv + i, kv = ceil(T / blockDim) <= KV), the per-thread round sums
 // are scanned two rounds per 32-bit word (sums < 2^16 per block: counts are
-// below 64 and blockDim * kv <= 1024), thread 0 makes one size reservation
-// for the pass -- clipped at `target`, and, if the pool cannot hold the
-// buckets it reaches, cut back to the longest prefix of whole rounds that
-// fits -- and takes the buckets (Algorithm 2); then (synchronize) the values
-// go to a shared-memory stage at their positions and the block streams the
-// stage to the buckets with aligned 128-bit stores (a pass larger than the
-// stage writes straight to the buckets).  Elements past the target are the
-// ones a round-by-round growth would clip (positions are round-major).
+// below 64 and blockDim * kv <= 1024), warp 0 scans the warp totals and its
+// lane 0 makes one size reservation for the pass -- clipped at `target`,
+// and, if the pool cannot hold the buckets it reaches, cut back to the
+// longest prefix of whole rounds that fits -- and takes the buckets
+// (Algorithm 2); then (synchronize) the values go to a shared-memory stage
+// at their positions and the block streams the stage to the buckets with
+// aligned 128-bit stores (a pass larger than the stage writes straight to
+// the buckets).  Elements past the target are the ones a round-by-round
+// growth would clip (positions are round-major).  The LFVector's bucket
+// table is kept in shared memory, so the write-out finds a bucket's
+// address without a global load.
 
 __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
   const int lane = threadIdx.x & 31;
@@ -175,24 +238,28 @@ __device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v) {
   return v;
 }
 
-struct GenShared {
-  uint32_t wt[4][32];   // packed warp prefixes (K / 2 <= 4 words)
-  uint32_t rb[9];       // pass-relative start of every round (K <= 8)
-  uint64_t base;        // LFVector size before the pass
-  uint32_t commit, nb;
-  int stop;             // 1: pool exhausted, 2: target reached
-};
-
-template <int E>
-__device__ __forceinline__ void put_gen_elem(uint64_t addr, typename Elem<E>::T x) {
-  *reinterpret_cast<typename Elem<E>::T*>(addr) = x;
+// Largest count a distribution draws (0 when it has no small bound).
+template <int DIST>
+__host__ __device__ constexpr uint32_t max_count() {
+  return DIST == GGA_DIST_BERNOULLI ? 1u : (DIST == GGA_DIST_UNIFORM3 ? 2u : 0u);
 }
 
-// Returns the number of rounds it drew.  Every thread of the block calls it.
-// SEARCH as for gen_count (g in shared memory).
-template <int E, int K, int KV, bool SEARCH = false>
+struct GenShared {
+  uint32_t wt[4][32];         // packed warp prefixes (K / 2 <= 4 words)
+  uint32_t rb[9];             // pass-relative start of every round (K <= 8)
+  uint64_t base;              // LFVector size before the pass
+  uint32_t commit, nb;
+  int stop;                   // 1: pool exhausted, 2: target reached
+  uint64_t tab[kMaxBuckets];  // the LFVector's bucket table (copy)
+};
+
+// Returns the number of rounds it drew; *done is set when the LFVector
+// reached `target` or the pool ran out.  Every thread of the block calls
+// it.  SEARCH as for gen_count (g in shared memory); DIST as for
+// gen_count_state (-1: g.dist at run time).
+template <int E, int K, int KV, bool SEARCH = false, int DIST = -1>
 __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t l, uint32_t R, uint64_t target,
-                                GenShared& sh, uint4* stage4, uint32_t cap) {
+                                GenShared& sh, uint4* stage4, uint32_t cap, bool* done) {
   typedef typename Elem<E>::T T;
   constexpr uint32_t VEC = 16 / E;
   constexpr int KP = K / 2;
@@ -204,17 +271,28 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
   const uint64_t tfirst = static_cast<uint64_t>(t0) * kv;        // first virtual thread
   const uint64_t gfirst = static_cast<uint64_t>(l) * v.T + tfirst;
   const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
-  const bool group_ok = v.B >= VEC;
+  const RoundDraws d0(g.seed, gfirst), d1(g.seed, gfirst + 1);   // virtual threads gfirst, gfirst + 1
   if (t0 == 0) {
     sh.base = v.sizes[l];
     sh.nb = v.nbuckets[l];
     sh.stop = sh.base >= target ? 2 : 0;
   }
+  {
+    const uint32_t nb0 = v.nbuckets[l];
+    for (uint32_t i = t0; i < nb0; i += NT) sh.tab[i] = bk[i];
+  }
   __syncthreads();
   uint32_t r0 = 0;
   while (r0 < R && sh.stop == 0) {
     const uint32_t kk = min(static_cast<uint32_t>(K), R - r0);
-    uint32_t pk[KP], inc[KP], cc[K];
+    // pk: the thread's per-round sums, two rounds per word.  c0w: with two
+    // virtual threads, the first one's count of round k in byte k % 4 of
+    // word k / 4 (the second's is the sum minus it); with one, the count is
+    // pk's half-word.
+    constexpr int KC = KV > 1 ? (K + 3) / 4 : 1;
+    uint32_t pk[KP], inc[KP], c0w[KC];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) c0w[q] = 0;
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       uint32_t c[2];
@@ -224,11 +302,10 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
         uint32_t c0 = 0, c1 = 0;
         if (k < kk) {
-          if (tfirst < v.T) c0 = gen_count<SEARCH>(g, splitmix(g.seed, (r << 32) | gfirst));
-          if (KV > 1 && kv > 1 && tfirst + 1 < v.T)
-            c1 = gen_count<SEARCH>(g, splitmix(g.seed, (r << 32) | (gfirst + 1)));
+          if (tfirst < v.T) c0 = gen_count_state<SEARCH, DIST>(g, d0.state(r));
+          if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = gen_count_state<SEARCH, DIST>(g, d1.state(r));
         }
-        cc[k] = c0 | (c1 << 8);
+        if (KV > 1) c0w[KV > 1 ? k / 4 : 0] |= c0 << (8 * (k % 4));
         c[h] = c0 + c1;
       }
       pk[j] = c[0] | (c[1] << 16);
@@ -261,6 +338,7 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
           const uint32_t need = buckets_for(base + commit, v.log2B);
           if (need > nb) {
             const uint32_t got = grow_buckets(v, l, nb, need);
+            for (uint32_t i = nb; i < got; ++i) sh.tab[i] = bk[i];
             sh.nb = got;
             v.nbuckets[l] = got;
             if (got < need) {
@@ -284,6 +362,15 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
     const uint32_t commit = sh.commit;
     const uint32_t shv = static_cast<uint32_t>(base & (VEC - 1));   // stage index = pass position + shv
     const bool staged = commit + shv <= cap;
+    // Fast path (block-uniform): the whole pass is kept and staged, so no
+    // element needs the clipping test or the bucket math.
+    const bool whole = staged && commit == sh.rb[K];
+    typedef typename std::conditional<E == 4, uint32_t, uint64_t>::type V;
+    // Element m of virtual thread i in round k: va * gid + vb * round + vc * m
+    // (a 4-byte element keeps the low 32 bits, which 32-bit arithmetic gives
+    // exactly).
+    const V vr = static_cast<V>(g.va) * static_cast<V>(gfirst) +
+                 static_cast<V>(g.vb) * static_cast<V>(static_cast<uint64_t>(g.round0) + r0);
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       const uint32_t ex = sh.wt[j][warp] + inc[j] - pk[j];
@@ -293,23 +380,28 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         uint32_t st = sh.rb[k] + ((ex >> (16 * h)) & 0xFFFFu);
 #pragma unroll
         for (int i = 0; i < KV; ++i) {
-          const uint32_t c = (cc[k] >> (8 * i)) & 0xFFu;
-          if (c == 0) continue;
-          // A 4-byte element keeps the low 32 bits of the value, which
-          // 32-bit arithmetic gives exactly.
-          typedef typename std::conditional<E == 4, uint32_t, uint64_t>::type V;
-          V val = static_cast<V>(g.va) * static_cast<V>(gfirst + i) +
-                  static_cast<V>(g.vb) * static_cast<V>(static_cast<uint64_t>(g.round0) + r0 + k);
-          for (uint32_t m = 0; m < c; ++m, val += static_cast<V>(g.vc)) {
-            const uint32_t q = st + m;
-            if (q >= commit) break;
-            if (staged) {
-              stage[q + shv] = gen_value<E>(val);
-            } else {
-              uint32_t bb;
-              uint64_t off;
-              bucket_of(base + q, v.log2B, bb, off);
-              put_gen_elem<E>(bk[bb] + off * E, gen_value<E>(val));
+          const uint32_t csum = (pk[j] >> (16 * h)) & 0xFFFFu;
+          const uint32_t cfirst = KV > 1 ? (c0w[KV > 1 ? k / 4 : 0] >> (8 * (k % 4))) & 0xFFu : csum;
+          const uint32_t c = i == 0 ? cfirst : csum - cfirst;
+          V val = vr + static_cast<V>(g.va) * static_cast<V>(i) + static_cast<V>(g.vb) * static_cast<V>(k);
+          if (whole && DIST >= 0 && max_count<DIST>() > 0 && max_count<DIST>() <= 2) {
+            // At most two elements: predicated stores, no loop.
+            if (c > 0) stage[st + shv] = gen_value<E>(val);
+            if (max_count<DIST>() > 1 && c > 1) stage[st + 1 + shv] = gen_value<E>(val + static_cast<V>(g.vc));
+          } else if (whole) {
+            for (uint32_t m = 0; m < c; ++m, val += static_cast<V>(g.vc)) stage[st + m + shv] = gen_value<E>(val);
+          } else {
+            for (uint32_t m = 0; m < c; ++m, val += static_cast<V>(g.vc)) {
+              const uint32_t q = st + m;
+              if (q >= commit) break;
+              if (staged) {
+                stage[q + shv] = gen_value<E>(val);
+              } else {
+                uint32_t bb;
+                uint64_t off;
+                bucket_of(base + q, v.log2B, bb, off);
+                reinterpret_cast<T*>(sh.tab[bb])[off] = gen_value<E>(val);
+              }
             }
           }
           st += c;
@@ -317,38 +409,17 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
       }
     }
     __syncthreads();
-    if (staged && commit) {
-      const uint64_t gbeg = base - shv;
-      const uint32_t nvec = (commit + shv + VEC - 1) / VEC;
-      for (uint32_t vi = t0; vi < nvec; vi += NT) {
-        const uint64_t p = gbeg + static_cast<uint64_t>(vi) * VEC;
-        const uint32_t lo = vi * VEC;   // stage index of p
-        if (group_ok && lo >= shv && lo + VEC <= commit + shv) {
-          uint32_t bb;
-          uint64_t off;
-          bucket_of(p, v.log2B, bb, off);
-          __stcs(reinterpret_cast<uint4*>(bk[bb] + off * E), stage4[vi]);
-        } else {
-#pragma unroll
-          for (uint32_t e = 0; e < VEC; ++e) {
-            const uint32_t si = lo + e;
-            if (si < shv || si >= commit + shv) continue;
-            uint32_t bb;
-            uint64_t off;
-            bucket_of(p + e, v.log2B, bb, off);
-            put_gen_elem<E>(bk[bb] + off * E, stage[si]);
-          }
-        }
-      }
-    }
+    if (staged && commit) stage_to_buckets<T>(sh.tab, v.log2B, v.B, base, commit, shv, stage4, t0, NT);
     // No barrier here: the next pass writes the stage, sh.wt, sh.rb and
     // sh.commit only after its first two barriers, which every thread reaches
     // after finishing this pass; sh.base is written by thread 0 and read by
     // thread 0 (the leader) before the next pass's second barrier and by the
-    // others after it; sh.stop was set before this pass's second barrier.
+    // others after it; sh.stop was set before this pass's second barrier;
+    // sh.tab only gains entries past those this pass reads.
     if (t0 == 0) sh.base = base + commit;
     r0 += kk;
   }
+  *done = sh.stop != 0;
   __syncthreads();   // the caller may reuse the stage and sh
   return r0;
 }

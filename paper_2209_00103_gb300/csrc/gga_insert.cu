@@ -796,49 +796,81 @@ int launch_finalize(const ArrayView& v, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // In-kernel generated insertion.
 
-// A pass's values are staged in 48 KB of shared memory (a pass averages 16
-// KB at K = 8 rounds, 512 threads, one int32 per thread and round; a pass
-// that does not fit writes directly).  Blocks of up to 512 threads are
-// compiled for 3 resident per SM (40 registers): measured on GB300 for 1024
-// blocks x 512 threads x 512 rounds, 1.29 ms against 1.43 ms with 64 KB and
-// the default register budget (2 resident), and 1.35 ms at 4 (spills).
+// A pass's values are staged in shared memory (a pass averages 16 KB at
+// K = 8 rounds, 512 threads, one int32 per thread and round; a pass that
+// does not fit writes directly).  Blocks of up to 512 threads are compiled
+// for 3 resident per SM (40 registers) with a 48 KB stage: measured on
+// GB300 for 1024 blocks x 512 threads x 512 rounds, 1.29 ms against 1.43 ms
+// with 64 KB and the default register budget (2 resident), and 1.35 ms at
+// 4 (spills).  GGA_GEN_VT = 1 plays T in (256, 512] with half as many
+// threads, two virtual threads each (one scan word covers both), and
+// GGA_GEN_MINB_VT resident blocks with a 32 KB stage.
+#ifndef GGA_GEN_VT
+#define GGA_GEN_VT 0
+#endif
+#ifndef GGA_GEN_MINB_VT
+#define GGA_GEN_MINB_VT 6
+#endif
+#ifndef GGA_GEN_MINB512
+#define GGA_GEN_MINB512 3
+#endif
+#ifndef GGA_GEN_STAGE_VT
+#define GGA_GEN_STAGE_VT 32768
+#endif
 constexpr uint32_t kGenStageBytes = 49152;
-constexpr int kGenMinBlocks512 = 3;
+constexpr uint32_t kGenStageBytesVT = GGA_GEN_STAGE_VT;
 
 template <int E> struct GenK { static constexpr int value = E == 16 ? 4 : 8; };
 
 // One block per LFVector, R rounds in passes of K (grow_passes in
 // gga_gen.cuh), with no target.
-template <int E, int K, int MAXT, int MINB>
-__global__ void __launch_bounds__(MAXT, MINB) gen_insert_kernel(ArrayView v, GenParams g, uint32_t R) {
+template <int E, int K, int KV, int MAXT, int MINB, int DIST>
+__global__ void __launch_bounds__(MAXT, MINB) gen_insert_kernel(const __grid_constant__ ArrayView v,
+                                                                const __grid_constant__ GenParams g, uint32_t R,
+                                                                uint32_t stage_bytes) {
   extern __shared__ uint4 s_stage4[];
   __shared__ GenShared sh;
-  grow_passes<E, K, 1>(v, g, blockIdx.x, R, ~0ull, sh, s_stage4, kGenStageBytes / E);
+  bool done;
+  grow_passes<E, K, KV, false, DIST>(v, g, blockIdx.x, R, ~0ull, sh, s_stage4, stage_bytes / E, &done);
 }
 
 int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32_t R, uint32_t* /*done*/,
                             int /*num_sms*/, cudaStream_t st) {
   const GenParams g = make_gen_params(spec);
-  const uint32_t NT = (v.T + 31) / 32 * 32;
-  const size_t smem = kGenStageBytes;
-#define GGA_GEN_AS(EE, KK, MT, MB)                                                                           \
+  const bool vt = GGA_GEN_VT && v.T > 256 && v.T <= 512;
+  const uint32_t NT = vt ? ((v.T + 1) / 2 + 31) / 32 * 32 : (v.T + 31) / 32 * 32;
+  const size_t smem = vt ? kGenStageBytesVT : kGenStageBytes;
+#define GGA_GEN_AD(EE, KK, KV, MT, MB, DD)                                                                   \
   do {                                                                                                       \
-    cudaFuncSetAttribute(gen_insert_kernel<EE, KK, MT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                         static_cast<int>(smem));                                                            \
-    gen_insert_kernel<EE, KK, MT, MB><<<v.L, NT, smem, st>>>(v, g, R);                                       \
+    cudaFuncSetAttribute(gen_insert_kernel<EE, KK, KV, MT, MB, DD>,                                          \
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));               \
+    gen_insert_kernel<EE, KK, KV, MT, MB, DD><<<v.L, NT, smem, st>>>(v, g, R, static_cast<uint32_t>(smem));   \
+  } while (0)
+  // The count distribution is a template argument: the draw loop then has
+  // no per-draw dispatch.
+#define GGA_GEN_AS(EE, KK, KV, MT, MB)                                                                       \
+  do {                                                                                                       \
+    switch (g.dist) {                                                                                        \
+      case GGA_DIST_BERNOULLI: GGA_GEN_AD(EE, KK, KV, MT, MB, GGA_DIST_BERNOULLI); break;                    \
+      case GGA_DIST_UNIFORM3: GGA_GEN_AD(EE, KK, KV, MT, MB, GGA_DIST_UNIFORM3); break;                      \
+      case GGA_DIST_GEOMETRIC: GGA_GEN_AD(EE, KK, KV, MT, MB, GGA_DIST_GEOMETRIC); break;                    \
+      default: GGA_GEN_AD(EE, KK, KV, MT, MB, GGA_DIST_POISSON); break;                                      \
+    }                                                                                                        \
   } while (0)
   // Rounds per pass: a pass then averages <= 32 KB at one element per thread
   // and round (K halves for blocks of more than 512 threads beyond 4 bytes).
 #define GGA_GEN(EE)                                                                                          \
   do {                                                                                                       \
-    if (NT <= 512) GGA_GEN_AS(EE, GenK<EE>::value, 512, kGenMinBlocks512);                                  \
-    else GGA_GEN_AS(EE, (EE == 4 ? 8 : GenK<EE>::value / 2), 1024, 1);                                       \
+    if (vt) GGA_GEN_AS(EE, GenK<EE>::value, 2, 256, GGA_GEN_MINB_VT);                                        \
+    else if (NT <= 512) GGA_GEN_AS(EE, GenK<EE>::value, 1, 512, GGA_GEN_MINB512);                            \
+    else GGA_GEN_AS(EE, (EE == 4 ? 8 : GenK<EE>::value / 2), 1, 1024, 1);                                    \
   } while (0)
   if (v.E == 4) GGA_GEN(4);
   else if (v.E == 8) GGA_GEN(8);
   else GGA_GEN(16);
 #undef GGA_GEN
 #undef GGA_GEN_AS
+#undef GGA_GEN_AD
   finalize_kernel<<<1, 1024, 0, st>>>(v);
   return cudaGetLastError() == cudaSuccess ? GGA_OK : GGA_ERR_CUDA;
 }

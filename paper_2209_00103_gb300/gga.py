@@ -34,7 +34,7 @@ MAX_THRESHOLDS = 16
 
 # Every symbol include/gga.h declares.
 EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gga_insert_generated",
-            "gga_device_view", "gga_device_commit", "gga_push_generated", "gga_read", "gga_write", "gga_sweep",
+            "gga_device_view", "gga_device_commit", "gga_push_generated", "gga_push_expand", "gga_read", "gga_write", "gga_sweep",
             "gga_flatten", "gga_size", "gga_offsets", "gga_clear", "gga_memory", "gga_last_error",
             "gga_destroy", "gga_twophase_spawn", "gga_twophase_work", "gga_pool_create", "gga_pool_destroy",
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
@@ -99,6 +99,7 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_device_view": [vp, ctypes.POINTER(vp)],
         "gga_device_commit": [vp, vp],
         "gga_push_generated": [vp, ctypes.POINTER(gga_gen_spec), u32, vp],
+        "gga_push_expand": [vp, vp, vp, u32, vp],
         "gga_read": [vp, vp, u64, vp, vp],
         "gga_write": [vp, vp, u64, vp, vp],
         "gga_sweep": [vp, i32, u64, u32, vp],
@@ -273,6 +274,16 @@ def gga_device_commit(h, stream=None):
 def gga_push_generated(h, spec: gga_gen_spec, rounds: int, stream=None):
     _check(load_library().gga_push_generated(h, ctypes.byref(spec), rounds, _stream(stream)),
            "gga_push_generated")
+
+
+def gga_push_expand(h, counts: torch.Tensor, inputs: torch.Tensor, stream=None):
+    """counts: uint32/int32 [R][L][T]; inputs: [R][L][T] elements of E bytes
+    (for E = 16, int64 [R][L][T][2]): thread t of block l appends
+    counts[r][l][t] copies of inputs[r][l][t] in round r."""
+    assert counts.dtype in (torch.int32, torch.uint32) and counts.dim() == 3
+    assert inputs.shape[:3] == counts.shape
+    _check(load_library().gga_push_expand(h, _dptr(counts), _dptr(inputs), counts.shape[0], _stream(stream)),
+           "gga_push_expand")
 
 
 def gga_read(h, idx: torch.Tensor, out: torch.Tensor, stream=None):
@@ -515,6 +526,10 @@ class GGArray:
     def push_generated(self, spec, rounds, stream=None):
         """insert_generated through the device API, one block_push_back per round."""
         gga_push_generated(self.h, spec, rounds, stream)
+
+    def push_expand(self, counts, inputs, stream=None):
+        """Memory-sourced pushes through the device API (block_push_rounds)."""
+        gga_push_expand(self.h, counts, inputs, stream)
 
     def read(self, idx, out=None, stream=None):
         if out is None:

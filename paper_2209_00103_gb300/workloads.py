@@ -163,6 +163,18 @@ class InsertSpec:
         return c, self.values(c)
 
 
+def expand_inputs(spec: "InsertSpec") -> np.ndarray:
+    """Per-(round, block, thread) inputs [R][L][T] of the memory-sourced
+    pushes: the value va*gtid + vb*r, E bytes each.  With spec.coeffs[2] = 0
+    the spec's packed values are these inputs repeated count times."""
+    r = np.arange(spec.round0, spec.round0 + spec.rounds, dtype=np.uint64)
+    gtid = np.uint64(spec.gtid0) + np.arange(spec.L * spec.T, dtype=np.uint64)
+    va, vb = (np.uint64(int(c) & MASK64) for c in spec.coeffs[:2])
+    with np.errstate(over="ignore"):
+        v = (va * gtid[None, :] + vb * r[:, None]).reshape(-1)
+    return encode_values(v, spec.E)
+
+
 def uniform_indices(seed: int, n: int, size: int) -> np.ndarray:
     """n indices uniform over [0, size) (size < 2^32): floor(u32 * size / 2^32)."""
     assert 0 < size < (1 << 32)
@@ -303,6 +315,18 @@ def make_insert_inputs_t(spec: "InsertSpec", device):
     va, vb, vc = (_s64(int(c)) for c in spec.coeffs)
     v = va * g_rep + vb * r_rep + vc * k
     return counts.reshape(R, spec.L, spec.T), encode_values_t(v, spec.E)
+
+
+def expand_inputs_t(spec: "InsertSpec", device):
+    """expand_inputs on `device`: [R][L][T] elements (int32 / int64, or
+    int64 pairs for 16-byte records)."""
+    import torch
+    r = torch.arange(spec.round0, spec.round0 + spec.rounds, dtype=torch.int64, device=device)
+    gtid = torch.arange(spec.L * spec.T, dtype=torch.int64, device=device)
+    va, vb = (_s64(int(c)) for c in spec.coeffs[:2])
+    v = (va * gtid[None, :] + vb * r[:, None]).reshape(-1)
+    e = encode_values_t(v, spec.E)
+    return e.reshape((spec.rounds, spec.L, spec.T) + tuple(e.shape[1:]))
 
 
 def uniform_indices_t(seed: int, n: int, size: int, device):

@@ -54,6 +54,66 @@ __global__ void __launch_bounds__(1024) push_rounds_cursor(const gga_dev_view* v
   }
 }
 
+// The same rounds through the other forms of the device API: mode 2, a
+// BlockPusher with a shared-memory stage (staged 128-bit writes); mode 3,
+// block_push_rounds with K = 4 rounds per call and a stage; mode 4,
+// block_push_rounds with K = 3 and no stage.  A block_push_rounds call
+// that keeps fewer than K rounds counts as a failed push.
+template <class T, int K>
+__device__ void push_rounds_k(const gga_dev_view* v, const uint32_t* counts, const T* vals, uint64_t* first,
+                              uint32_t R, uint32_t L, uint32_t NT, uint32_t kmax, uint32_t l, int stop_on_fail,
+                              void* stage, uint32_t stage_bytes) {
+  const uint32_t t = gga::block_rank();
+  for (uint32_t r0 = 0; r0 < R; r0 += K) {
+    uint32_t c[K];
+    const T* mine[K];
+    for (int k = 0; k < K; ++k) {
+      const uint32_t r = r0 + k;
+      const uint64_t row = (static_cast<uint64_t>(r < R ? r : 0) * L + l) * NT + t;
+      c[k] = r < R ? counts[row] : 0u;
+      mine[k] = vals + row * kmax;
+    }
+    uint64_t j0[K];
+    const uint32_t done = gga::block_push_rounds<T, K>(
+        v, l, c, [&](uint32_t kr, uint32_t k) { return mine[kr][k]; }, stage, stage_bytes, j0);
+    for (int k = 0; k < K; ++k) {
+      const uint32_t r = r0 + k;
+      if (r < R) first[(static_cast<uint64_t>(r) * L + l) * NT + t] = static_cast<uint32_t>(k) < done ? j0[k] : ~0ull;
+    }
+    if (done < static_cast<uint32_t>(K) && stop_on_fail) break;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) push_rounds_mode(const gga_dev_view* v, const uint32_t* counts,
+                                                         const T* vals, uint64_t* first, uint32_t R, uint32_t L,
+                                                         uint32_t NT, uint32_t kmax, int reverse, int stop_on_fail,
+                                                         int mode, uint32_t stage_bytes) {
+  __shared__ gga::PushShared sh;
+  extern __shared__ uint4 stage[];
+  const uint32_t t = gga::block_rank();
+  for (uint32_t i = blockIdx.x; i < L; i += gridDim.x) {
+    const uint32_t l = reverse ? L - 1 - i : i;
+    if (mode == 2) {
+      gga::BlockPusher<T> pusher(v, l, sh, stage, stage_bytes);
+      for (uint32_t r = 0; r < R; ++r) {
+        const uint64_t row = (static_cast<uint64_t>(r) * L + l) * NT + t;
+        const T* mine = vals + row * kmax;
+        uint64_t j0 = ~0ull;
+        const bool ok = pusher.push(counts[row], [&](uint32_t k) { return mine[k]; }, &j0);
+        first[row] = ok ? j0 : ~0ull;
+        if (!ok && stop_on_fail) break;
+      }
+      pusher.flush();
+    } else if (mode == 3) {
+      push_rounds_k<T, 4>(v, counts, vals, first, R, L, NT, kmax, l, stop_on_fail, stage, stage_bytes);
+    } else {
+      push_rounds_k<T, 3>(v, counts, vals, first, R, L, NT, kmax, l, stop_on_fail, nullptr, 0);
+    }
+    __syncthreads();   // the next LFVector's pushes reuse the shared slots and the stage
+  }
+}
+
 // Rounds whose values are a formula of (round, LFVector, thread, k), for
 // counts too large to hold their values in an array: element k of thread t
 // of LFVector l in round r is (r << 56) | (l << 48) | (t << 32) | k.
@@ -153,6 +213,32 @@ int user_push_rounds_cursor(const void* view, const uint32_t* counts, const void
   else
     push_rounds_cursor<uint4><<<blocks, block, 0, st>>>(v, counts, static_cast<const uint4*>(vals), first, R, L, nt,
                                                         kmax, reverse, stop_on_fail);
+  return launched();
+}
+
+int user_push_rounds_mode(const void* view, const uint32_t* counts, const void* vals, uint64_t* first, uint32_t R,
+                          uint32_t L, uint32_t bx, uint32_t by, uint32_t kmax, uint32_t E, uint32_t blocks,
+                          int reverse, int stop_on_fail, int mode, uint32_t stage_bytes, void* stream) {
+  const gga_dev_view* v = static_cast<const gga_dev_view*>(view);
+  const dim3 block(bx, by);
+  const uint32_t nt = bx * by;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t smem = stage_bytes;
+  if (E == 4) {
+    cudaFuncSetAttribute(push_rounds_mode<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_bytes);
+    push_rounds_mode<uint32_t><<<blocks, block, smem, st>>>(v, counts, static_cast<const uint32_t*>(vals), first, R,
+                                                            L, nt, kmax, reverse, stop_on_fail, mode, stage_bytes);
+  } else if (E == 8) {
+    cudaFuncSetAttribute(push_rounds_mode<unsigned long long>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         stage_bytes);
+    push_rounds_mode<unsigned long long><<<blocks, block, smem, st>>>(
+        v, counts, static_cast<const unsigned long long*>(vals), first, R, L, nt, kmax, reverse, stop_on_fail, mode,
+        stage_bytes);
+  } else {
+    cudaFuncSetAttribute(push_rounds_mode<uint4>, cudaFuncAttributeMaxDynamicSharedMemorySize, stage_bytes);
+    push_rounds_mode<uint4><<<blocks, block, smem, st>>>(v, counts, static_cast<const uint4*>(vals), first, R, L, nt,
+                                                         kmax, reverse, stop_on_fail, mode, stage_bytes);
+  }
   return launched();
 }
 

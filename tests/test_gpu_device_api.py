@@ -57,23 +57,34 @@ def expected_first(counts, size0):
     return before[..., None] + np.cumsum(c, axis=2) - c
 
 
-def push(user, g, counts, vals, bx, by, kmax, blocks=None, reverse=0, stop_on_fail=1, cursor=False):
-    """The rounds through block_push_back calls, or (cursor) a BlockPusher."""
+# Forms of the device API a user kernel pushes through: 0 block_push_back per
+# round, 1 a BlockPusher, 2 a BlockPusher with a shared-memory stage (staged
+# 128-bit writes), 3 block_push_rounds, 4 rounds per call, staged, 4
+# block_push_rounds, 3 rounds per call, unstaged.
+FORMS = [0, 1, 2, 3, 4]
+STAGE_BYTES = 8192   # small enough that large pushes take the unstaged path
+
+
+def push(user, g, counts, vals, bx, by, kmax, blocks=None, reverse=0, stop_on_fail=1, cursor=0):
+    """The rounds through the device-API form `cursor` (FORMS)."""
     R, L, NT = counts.shape
     assert bx * by == NT and vals.shape[0] == R * L * NT * kmax
     cd = counts_to_dev(counts)
     vd = values_to_dev(vals, g.E)
     first = torch.empty(R * L * NT, dtype=torch.int64, device="cuda")
-    fn = user.user_push_rounds_cursor if cursor else user.user_push_rounds
-    rc = fn(ctypes.c_void_p(g.device_view()), ctypes.c_void_p(cd.data_ptr()), ctypes.c_void_p(vd.data_ptr()),
-            ctypes.c_void_p(first.data_ptr()), R, L, bx, by, kmax, g.E, blocks or L, reverse, stop_on_fail,
-            stream_ptr())
+    args = (ctypes.c_void_p(g.device_view()), ctypes.c_void_p(cd.data_ptr()), ctypes.c_void_p(vd.data_ptr()),
+            ctypes.c_void_p(first.data_ptr()), R, L, bx, by, kmax, g.E, blocks or L, reverse, stop_on_fail)
+    if int(cursor) >= 2:
+        rc = user.user_push_rounds_mode(*args, int(cursor), STAGE_BYTES, stream_ptr())
+    else:
+        fn = user.user_push_rounds_cursor if cursor else user.user_push_rounds
+        rc = fn(*args, stream_ptr())
     assert rc == 0
     g.device_commit()
     return first.cpu().numpy().view(np.uint64).reshape(R, L, NT)
 
 
-@pytest.mark.parametrize("cursor", [False, True])
+@pytest.mark.parametrize("cursor", FORMS)
 @pytest.mark.parametrize("E", [4, 8, 16])
 @pytest.mark.parametrize("bx,by", [(128, 1), (100, 1), (16, 6), (1, 1), (1024, 1), (8, 4), (33, 31)])
 def test_user_kernel_pushes_match_oracle(user, E, bx, by, cursor):
@@ -119,7 +130,7 @@ def test_device_pushes_and_library_insertions_interleave(user):
     g.close()
 
 
-@pytest.mark.parametrize("cursor", [False, True])
+@pytest.mark.parametrize("cursor", FORMS)
 def test_grid_stride_blocks_and_reversed_lfvectors(user, cursor):
     # Fewer blocks than LFVectors, each block serving several in reverse
     # (with cursors: one after another on the same shared slots).
@@ -215,7 +226,7 @@ def round_chunks(counts, packed, l):
     return [packed[start[r * L + l]:start[r * L + l + 1]] for r in range(R)]
 
 
-@pytest.mark.parametrize("cursor", [False, True])
+@pytest.mark.parametrize("cursor", FORMS)
 @pytest.mark.parametrize("stop_on_fail", [1, 0])
 def test_pool_exhaustion_keeps_whole_rounds(user, stop_on_fail, cursor):
     # A pool too small for every LFVector: a block whose buckets do not fit
@@ -419,3 +430,82 @@ def test_pushes_into_arrays_of_one_shared_pool_reuse_cleared_buckets(user):
     b.close()
     a.close()
     pool.close()
+
+
+# ---------------------------------------------------------------------------
+# gga_push_expand: values read from device memory, pushed K rounds per call
+# through gga::block_push_rounds (staged, 128-bit stores).
+
+def expand_case(L, T, E, R, seed, dist="uniform3", round0=0):
+    spec = wl.InsertSpec(L=L, T=T, E=E, seed=seed, dist=dist, rounds=R, round0=round0,
+                         coeffs=(7, 1 << 20, 0), thresholds=wl.poisson1_thresholds() if dist == "poisson" else None)
+    counts = spec.counts()
+    inputs = wl.expand_inputs(spec)
+    packed = spec.values(counts)   # the inputs repeated count times (vc = 0)
+    return counts, inputs, packed
+
+
+@pytest.mark.parametrize("E", [4, 8, 16])
+@pytest.mark.parametrize("T", [96, 300, 512])
+def test_push_expand_matches_oracle(T, E):
+    L, B = 13, 16
+    g, o = make_pair(L, T, B, E, pool_bytes=128 << 20)
+    for step, (R, dist) in enumerate([(11, "uniform3"), (1, "geometric"), (6, "poisson"), (17, "bernoulli")]):
+        counts, inputs, packed = expand_case(L, T, E, R, seed=40 + step, dist=dist, round0=3 * step)
+        g.push_expand(counts_to_dev(counts), values_to_dev(inputs, E).reshape(
+            (R, L, T) + ((2,) if E == 16 else ())))
+        o.insert(counts, packed)
+        assert g.last_error() == gga.GGA_OK
+        assert_same_state(g, o)
+    g.close()
+    o.close()
+
+
+def test_push_expand_pool_exhaustion_keeps_whole_leading_rounds():
+    # A pool too small: each LFVector keeps a prefix of whole rounds (the
+    # longest that fits in the call that failed) and stops there.
+    L, T, B, E, R = 16, 64, 16, 4, 24
+    counts, inputs, packed = expand_case(L, T, E, R, seed=9)
+    g = gga.GGArray(L, T, B, E, 64 << 10)
+    g.push_expand(counts_to_dev(counts), values_to_dev(inputs, E).reshape(R, L, T))
+    n, rc, sizes, caps = g.sizes_caps()
+    assert rc == gga.GGA_ERR_POOL_EXHAUSTED
+    sizes = sizes.cpu().numpy().astype(np.int64)
+    flat = dev_to_np(g.flatten(), E)[:n]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    per_round = counts.sum(axis=2).astype(np.int64)            # [R][L]
+    starts = np.concatenate([[0], np.cumsum(counts.reshape(-1).astype(np.int64))])
+    short = 0
+    for l in range(L):
+        cum = np.concatenate([[0], np.cumsum(per_round[:, l])])
+        kept = int(np.searchsorted(cum, sizes[l]))
+        assert cum[kept] == sizes[l], l                         # whole rounds only
+        want = b"".join(packed[starts[r * L * T + l * T]:starts[r * L * T + (l + 1) * T]].tobytes()
+                        for r in range(kept))
+        assert flat[offs[l]:offs[l + 1]].tobytes() == want, l
+        short += kept < R
+    assert short > 0
+    g.close()
+
+
+def test_push_expand_full_paper_size():
+    # The paper-shaped workload (1024 x 512, B = 4096, 512 rounds of
+    # Uniform{0,1,2}) through the memory-sourced device-API pushes, in the
+    # launch configuration bench.py times, against the oracle.
+    w = wl.paper_growth()
+    spec = wl.InsertSpec(L=w.L, T=w.T, E=w.E, seed=w.spec.seed, dist=w.spec.dist, rounds=w.spec.rounds,
+                         coeffs=(w.spec.coeffs[0], w.spec.coeffs[1], 0))
+    dev = torch.device("cuda", 0)
+    counts_t, values_t = wl.make_insert_inputs_t(spec, dev)
+    inputs_t = wl.expand_inputs_t(spec, dev)
+    N = int(values_t.shape[0])
+    g = gga.GGArray(w.L, w.T, w.B, w.E, 3 << 30)
+    g.push_expand(counts_t, inputs_t)
+    n, rc = g.size()
+    assert rc == gga.GGA_OK and n == N
+    o = oracle.OracleGGArray(w.L, w.T, w.B, w.E)
+    o.insert(counts_t.cpu().numpy().view(np.uint32), values_t.cpu().numpy().view(np.uint32))
+    del counts_t, values_t, inputs_t
+    assert_same_state(g, o)
+    g.close()
+    o.close()

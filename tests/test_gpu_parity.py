@@ -171,6 +171,23 @@ def test_generated_insert_matches_oracle(dist, E):
     g.close()
 
 
+@pytest.mark.parametrize("T", [300, 512, 1000])
+@pytest.mark.parametrize("dist,E", [("uniform3", 4), ("poisson", 16), ("geometric", 8)])
+def test_generated_insert_wide_blocks(T, dist, E):
+    # Blocks of more than 256 threads (the launches that may play two
+    # virtual threads per thread), ragged T, rounds not a multiple of a pass.
+    L, B = 37, 64
+    thr = wl.poisson1_thresholds()
+    coeffs = (3, 1 << 21, 7)
+    g, o = make_pair(L, T, B, E, pool_bytes=256 << 20)
+    for round0, R in [(0, 13), (13, 8)]:
+        spec = gga.make_gen_spec(5, dist, coeffs, round0=round0, thresholds=thr if dist == "poisson" else None)
+        g.insert_generated(spec, R)
+        o.insert_generated(5, dist, coeffs, round0, R, thresholds=thr)
+        assert_same_state(g, o)
+    g.close()
+
+
 def test_generated_and_packed_paths_agree():
     # The in-kernel generated insertion and gga_insert on the same draws.
     spec_np = wl.InsertSpec(L=32, T=256, E=4, seed=1, dist="bernoulli", rounds=10, coeffs=(10, 1, 0))

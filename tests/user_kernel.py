@@ -38,6 +38,7 @@ def load_user() -> ctypes.CDLL:
     sig = {
         "user_push_rounds": [vp, vp, vp, vp, u32, u32, u32, u32, u32, u32, u32, i32, i32, vp],
         "user_push_rounds_cursor": [vp, vp, vp, vp, u32, u32, u32, u32, u32, u32, u32, i32, i32, vp],
+        "user_push_rounds_mode": [vp, vp, vp, vp, u32, u32, u32, u32, u32, u32, u32, i32, i32, i32, u32, vp],
         "user_push_own": [vp, vp, vp, u32, u32, u32, vp],
         "user_push_formula": [vp, vp, u32, u32, u32, i32, vp],
         "user_read_global": [vp, vp, u64, vp, vp, u32, vp],
