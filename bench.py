@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--arrays", type=int, default=4096, help="batched: number of arrays (a smaller case for profiling)")
     ap.add_argument("--n0", type=int, default=1 << 24, help="two_phase: initial records (a smaller case for profiling)")
     ap.add_argument("--generations", type=int, default=8, help="two_phase: spawning generations")
+    ap.add_argument("--no-sweep", action="store_true", help="served: skip the arrival-rate sweep")
     ap.add_argument("--deadline", type=float, default=None,
                     help="served: seconds an append may wait for pool memory before it is rejected")
     return ap.parse_args()
@@ -820,6 +821,7 @@ def run_served(args, world, rank, local):
     plain = serving.Server(cfg)
     rep_plain = plain.run(trace, batched=False)
     plain.close()
+    sweep = None if args.no_sweep else served_load_sweep(serving)
     return {"metric": "served GGArray p99 latency (ms), continuous batching", "value": rep["p99_ms"], "unit": "ms",
             "n_gpus": world, "steps": rep["completed"], "warmup": 0,
             "ms_per_step": round(rep["wall_s"] * 1e3 / max(1, rep["completed"]), 5), "higher_is_better": False,
@@ -828,7 +830,45 @@ def run_served(args, world, rank, local):
                        "duration_s": cfg.duration, "requests": int(len(trace[0])), "arrays": cfg.n_arrays,
                        "L": cfg.L, "T": cfg.T, "B": cfg.B, "pool_bytes": cfg.pool_bytes,
                        "deadline_s": cfg.deadline, "max_inflight_steps": cfg.max_inflight},
-            "served": rep, "plain_one_launch_per_request": rep_plain, "clocks": clocks}
+            "served": rep, "plain_one_launch_per_request": rep_plain, "load_sweep": sweep, "clocks": clocks}
+
+
+SWEEP_RATES = (20000.0, 50000.0, 100000.0, 200000.0, 500000.0, 1000000.0)
+SWEEP_P99_BOUND_MS = 10.0
+
+
+def served_load_sweep(serving, rates=SWEEP_RATES, p99_bound_ms=SWEEP_P99_BOUND_MS):
+    """The same request mix at higher arrival rates, through both forms,
+    over the window before the pool fills: each rate runs for half the time
+    the offered appends (0.7 * rate * E[n] * 8 bytes per second, E[n] of the
+    log-uniform sizes) take to fill the 64 GiB pool, at most 2 s.  A form
+    sustains a rate when it completes every request with p99 latency at most
+    p99_bound_ms and finishes within 10% of the trace's duration."""
+    import math
+    base = serving.ServeConfig()
+    mean_n = (base.max_append - 1) / math.log(base.max_append)
+    points = []
+    for rate in rates:
+        fill_s = base.pool_bytes / (base.mix[0] * rate * mean_n * base.E)
+        cfg = serving.ServeConfig(rate=rate, duration=round(min(2.0, 0.5 * fill_s), 3))
+        trace = serving.make_trace(cfg)
+        point = {"rate_per_s": rate, "duration_s": cfg.duration, "requests": int(len(trace[0]))}
+        for name, batched in (("batched", True), ("plain", False)):
+            srv = serving.Server(cfg)
+            r = srv.run(trace, batched=batched)
+            srv.close()
+            ok = (r["completed"] == r["requests"] and r.get("p99_ms", math.inf) <= p99_bound_ms
+                  and r["wall_s"] <= 1.1 * cfg.duration)
+            point[name] = {"p50_ms": r.get("p50_ms"), "p99_ms": r.get("p99_ms"), "elements_per_s": r["elements_per_s"],
+                           "wall_s": r["wall_s"], "completed": r["completed"], "rejected": r["rejected"],
+                           "requests_per_step": r["mean_requests_per_step"], "sustained": bool(ok)}
+        points.append(point)
+    best = {}
+    for name in ("batched", "plain"):
+        ok = [p for p in points if p[name]["sustained"]]
+        best[name] = ({"rate_per_s": ok[-1]["rate_per_s"], "elements_per_s": ok[-1][name]["elements_per_s"]}
+                      if ok else None)
+    return {"p99_bound_ms": p99_bound_ms, "points": points, "highest_sustained": best}
 
 
 def run_two_phase(args, world, rank, local):

@@ -40,7 +40,7 @@ EXPORTED = ["gga_create", "gga_insert", "gga_insert_noalloc", "gga_reserve", "gg
             "gga_pool_info", "gga_create_in_pool", "gga_batch_create", "gga_batch_grow", "gga_batch_clear",
             "gga_batch_capture", "gga_batch_replay", "gga_batch_destroy", "gga_append_batch", "gga_read_batch",
             "gga_vmm_create", "gga_vmm_grow", "gga_vmm_info", "gga_vmm_destroy", "gga_flat_insert",
-            "gga_debug_wait_timeout"]
+            "gga_debug_wait_timeout", "gga_serve_run"]
 
 
 class gga_params(ctypes.Structure):
@@ -67,6 +67,22 @@ class gga_append_req(ctypes.Structure):
 class gga_read_req(ctypes.Structure):
     _fields_ = [("array", ctypes.c_void_p), ("n", ctypes.c_uint64), ("seed", ctypes.c_uint64),
                 ("out", ctypes.c_void_p)]
+
+
+class gga_serve_config(ctypes.Structure):
+    _fields_ = [("n_arrays", ctypes.c_uint32), ("L", ctypes.c_uint32), ("B", ctypes.c_uint32),
+                ("E", ctypes.c_uint32), ("read_n", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("batched", ctypes.c_int32), ("deadline_s", ctypes.c_double),
+                ("pool_bytes", ctypes.c_uint64)]
+
+
+class gga_serve_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("step_requests", ctypes.c_uint64),
+                ("appended_elements", ctypes.c_uint64), ("wall_s", ctypes.c_double),
+                ("first_full_s", ctypes.c_double)]
+
+
+SERVE_RESULT_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64)
 
 
 class gga_mem(ctypes.Structure):
@@ -123,6 +139,8 @@ def load_library(build_if_missing: bool = True) -> ctypes.CDLL:
         "gga_batch_destroy": [vp],
         "gga_append_batch": [ctypes.POINTER(gga_append_req), u32, vp],
         "gga_read_batch": [ctypes.POINTER(gga_read_req), u32, vp],
+        "gga_serve_run": [ctypes.POINTER(gga_serve_config), ctypes.POINTER(vp), u64, vp, vp, vp, vp, vp, vp, vp, u64,
+                          vp, vp, SERVE_RESULT_FN, vp, ctypes.POINTER(gga_serve_stats), vp],
         "gga_twophase_work": [vp, u64, u32, vp],
         "gga_flat_insert": [i32, vp, u64, vp, u64, u32, u32, vp],
         "gga_debug_wait_timeout": [u32, i32, vp],
@@ -366,6 +384,56 @@ def gga_read_batch(reqs, stream=None):
         arr[i].array, arr[i].n, arr[i].seed = g.h, int(n), int(seed) & 0xFFFFFFFFFFFFFFFF
         arr[i].out = out.data_ptr()
     _check(load_library().gga_read_batch(arr, len(reqs), _stream(stream)), "gga_read_batch")
+
+
+def gga_serve_run(cfg: gga_serve_config, handles, t, typ, arr, nn, tag, read_out, flat_arena, on_result=None,
+                  stream=None):
+    """Run a request trace through the native server (include/gga_serve.h).
+    t, typ, arr, nn, tag: host arrays (float64, int8, int64, int64, int64);
+    read_out, flat_arena: device int64 tensors; on_result(request, dev_ptr,
+    n_elems) or None.  Returns (latency_s, state, stats dict)."""
+    import numpy as np
+    m = len(t)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    typ = np.ascontiguousarray(typ, dtype=np.int8)
+    arr = np.ascontiguousarray(arr, dtype=np.int64)
+    nn = np.ascontiguousarray(nn, dtype=np.int64)
+    tag = np.ascontiguousarray(tag, dtype=np.int64)
+    lat = np.empty(m, dtype=np.float64)
+    state = np.zeros(m, dtype=np.int8)
+    hs = (ctypes.c_void_p * max(1, len(handles)))(*handles)
+    cb = SERVE_RESULT_FN(lambda ctx, r, ptr, n: on_result(int(r), int(ptr or 0), int(n))) if on_result else \
+        SERVE_RESULT_FN()
+    st = gga_serve_stats()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    arena_elems = flat_arena.numel() * flat_arena.element_size() // cfg.E
+    _check(load_library().gga_serve_run(ctypes.byref(cfg), hs, m, p(t), p(typ), p(arr), p(nn), p(tag),
+                                        _dptr(read_out), _dptr(flat_arena), arena_elems, p(lat), p(state), cb, None,
+                                        ctypes.byref(st), _stream(stream)), "gga_serve_run")
+    stats = {"steps": st.steps, "step_requests": st.step_requests, "appended_elements": st.appended_elements,
+             "wall_s": st.wall_s, "first_full_s": None if st.first_full_s < 0 else st.first_full_s}
+    return lat, state, stats
+
+
+_cudart = None
+
+
+def device_to_host(ptr: int, nbytes: int) -> bytes:
+    """Copy nbytes at device address ptr to the host (cudaMemcpy of the CUDA
+    runtime the library links; for test-mode result capture)."""
+    global _cudart
+    if _cudart is None:
+        import glob
+        cands = sorted(glob.glob(os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64", "libcudart.so*")))
+        if not cands:
+            raise ImportError("libcudart not found")
+        _cudart = ctypes.CDLL(cands[-1])
+    buf = ctypes.create_string_buffer(max(1, nbytes))
+    if nbytes:
+        rc = _cudart.cudaMemcpy(buf, ctypes.c_void_p(ptr), ctypes.c_size_t(nbytes), 2)   # device to host
+        if rc != 0:
+            raise GGAError(GGA_ERR_CUDA, "cudaMemcpy")
+    return buf.raw[:nbytes]
 
 
 def gga_debug_wait_timeout(attempts: int, arrive: bool, stream=None) -> int:

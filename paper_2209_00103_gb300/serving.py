@@ -24,6 +24,7 @@ The plain mode runs the same trace one request at a time, waiting for each.
 
 from __future__ import annotations
 
+import hashlib
 import heapq
 import math
 import time
@@ -157,7 +158,9 @@ class CudaBackend:
 class Server:
     LOOK_AHEAD = 32     # waiting appends tried per step after memory was freed
 
-    def __init__(self, cfg: ServeConfig, stream=None, record: bool = False, backend=None):
+    def __init__(self, cfg: ServeConfig, stream=None, record=False, backend=None):
+        """record: False, True (keep every read and flatten result), or
+        "digest" (keep the SHA-256 of each result's bytes)."""
         self.be = backend or CudaBackend()
         gga = self.gga = self.be.gga
         self.cfg = cfg
@@ -188,7 +191,15 @@ class Server:
                                  for b in range(buckets_for(s, cfg.B))])
 
     # -- the loop -----------------------------------------------------------
-    def run(self, trace, batched: bool = True):
+    def run(self, trace, batched: bool = True, native: bool | None = None):
+        """Serve the trace.  native (default: on the GPU) runs the same rules
+        in the library's native loop (gga_serve_run, include/gga_serve.h);
+        otherwise this Python loop runs them (it is also the model the
+        scheduling tests exercise with a fake device)."""
+        if native is None:
+            native = isinstance(self.be, CudaBackend)
+        if native:
+            return self._run_native(trace, batched)
         cfg = self.cfg
         t_arr, typ, arr, nn, tag = trace
         m = len(t_arr)
@@ -324,6 +335,39 @@ class Server:
         rep["mean_requests_per_step"] = round(batched_reqs / max(1, steps), 3)
         return rep
 
+    def _run_native(self, trace, batched: bool):
+        gga, cfg = self.gga, self.cfg
+        t_arr, typ, arr, nn, tag = trace
+        c = gga.gga_serve_config()
+        c.n_arrays, c.L, c.B, c.E = cfg.n_arrays, cfg.L, cfg.B, cfg.E
+        c.read_n, c.max_inflight, c.max_batch = cfg.read_n, cfg.max_inflight, cfg.max_batch
+        c.batched, c.deadline_s, c.pool_bytes = 1 if batched else 0, cfg.deadline, cfg.pool_bytes
+
+        def keep(r, ptr, n):
+            data = gga.device_to_host(ptr, n * cfg.E)
+            if self.record == "digest":
+                self.results[r] = hashlib.sha256(data).hexdigest()
+            else:
+                self.results[r] = np.frombuffer(data, dtype=np.int64).copy()
+
+        lat, state, st = gga.gga_serve_run(c, [a.g.h for a in self.arrays], t_arr, typ, arr, nn, tag,
+                                           self.read_out, self.flat_arena, keep if self.record else None,
+                                           self.stream)
+        self.latency, self.state = lat, state
+        rep = self._report(lat, state, typ, nn, st["wall_s"], st["appended_elements"])
+        t_full = math.inf if st["first_full_s"] is None else st["first_full_s"]
+        rep["pool_first_full_s"] = None if math.isinf(t_full) else round(float(t_full), 3)
+        for name, sel in (("before_pool_full", t_arr < t_full), ("after_pool_full", t_arr >= t_full)):
+            done = (state == 1) & sel
+            if done.any():
+                ms = lat[done] * 1e3
+                rep[name] = {"completed": int(done.sum()), "p50_ms": round(float(np.percentile(ms, 50)), 4),
+                             "p99_ms": round(float(np.percentile(ms, 99)), 4)}
+        rep["steps"] = st["steps"]
+        rep["mean_requests_per_step"] = round(st["step_requests"] / max(1, st["steps"]), 3)
+        rep["scheduler"] = "native"
+        return rep
+
     def _launch(self, appends, reads, flats, arr, nn, tag, slot, s):
         """Enqueue one step; returns where each read/flatten result lands."""
         gga = self.gga
@@ -362,13 +406,15 @@ class Server:
         return dst
 
     def _save(self, r, where):
-        # Test mode: keep read and flatten results once their step completed.
+        # Test mode: keep read and flatten results (or, with record="digest",
+        # the SHA-256 of their bytes) once their step completed.
         if where[0] == "read":
             _, sl, j = where
-            self.results[r] = self.read_out[sl, j].cpu().numpy().copy()
+            res = self.read_out[sl, j].cpu().numpy().copy()
         else:
             _, dst, n = where
-            self.results[r] = dst[:n].cpu().numpy().copy()
+            res = dst[:n].cpu().numpy().copy()
+        self.results[r] = hashlib.sha256(res.tobytes()).hexdigest() if self.record == "digest" else res
 
     def _report(self, lat, state, typ, nn, wall, appended):
         done = state == 1

@@ -11,7 +11,8 @@ import oracle
 from paper_2209_00103_gb300 import batching, gga
 from paper_2209_00103_gb300 import workloads as wl
 
-from harness import assert_same_state
+import oracle_pool
+from harness import assert_same_state, dev_to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -111,13 +112,25 @@ def test_batched_workload_4096_arrays():
     assert np.array_equal(got, sizes)                       # every array reached its target
     assert all(g.last_error() == gga.GGA_OK for g in arrays)
     assert batching.memory_ratio(arrays) <= 2.1
-    order = np.argsort(sizes)
-    sample = sorted(set([int(order[0]), int(order[1]), int(order[-1]), int(order[-2])] +
-                        np.random.default_rng(5).choice(len(sizes), 12, replace=False).tolist()))
+    # Every one of the 4096 arrays against the oracle (run in a spawned
+    # worker pool; each side reduced to a digest of its sizes, capacities,
+    # offsets and flattened contents).
     thr = wl.poisson1_thresholds()
-    for a in sample:
-        T, L, B = params[a]
-        o = oracle.OracleGGArray(L, T, B, batching.payload_bytes(a))
-        o.grow_to_target((3 << 32) | a, "poisson", (0x10001, 0x9E3779B9, 7), int(sizes[a]), thresholds=thr)
-        assert_same_state(arrays[a], o)
+    jobs = [(a, params[a][1], params[a][0], params[a][2], batching.payload_bytes(a), (3 << 32) | a, "poisson",
+             (0x10001, 0x9E3779B9, 7), int(sizes[a]), thr) for a in range(len(sizes))]
+    want = oracle_pool.grown_digests(jobs)
+    bad = []
+    for a, g in enumerate(arrays):
+        n, rc, s_, c_ = g.sizes_caps()
+        flat = dev_to_np(g.flatten(), g.E)[:n].tobytes() if n else b""
+        got = oracle_pool.state_digest(s_.cpu().numpy(), c_.cpu().numpy(), g.offsets().cpu().numpy(), flat)
+        if rc != gga.GGA_OK or got != want[a]:
+            bad.append(a)
+    assert not bad, bad[:10]
+    # One array in full, element by element (a failure there shows where).
+    a = int(np.argmax(sizes))
+    T, L, B = params[a]
+    o = oracle.OracleGGArray(L, T, B, batching.payload_bytes(a))
+    o.grow_to_target((3 << 32) | a, "poisson", (0x10001, 0x9E3779B9, 7), int(sizes[a]), thresholds=thr)
+    assert_same_state(arrays[a], o)
     batching.teardown(pool, arrays, batch)

@@ -13,7 +13,7 @@ import oracle
 from paper_2209_00103_gb300 import gga
 from paper_2209_00103_gb300 import workloads as wl
 
-from harness import assert_same_state, insert_both, make_pair, packed_values, random_counts, values_to_dev
+from harness import assert_same_state, dev_to_np, insert_both, make_pair, packed_values, random_counts, values_to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -53,4 +53,47 @@ def test_binned_writes_out_of_range_are_skipped_and_reported():
     assert o.write(idx, vals) == oracle.ERR_OUT_OF_RANGE
     assert g.last_error() == gga.GGA_ERR_OUT_OF_RANGE
     assert_same_state(g, o)                                         # every in-range write applied
+    g.close()
+
+
+def as_records(a: np.ndarray, E: int) -> np.ndarray:
+    """Elements as one comparable item each (16-byte records as two uint64)."""
+    if E == 16:
+        return np.ascontiguousarray(a).view(np.uint64).reshape(-1, 2)
+    return np.ascontiguousarray(a).view({4: np.uint32, 8: np.uint64}[E]).reshape(-1, 1)
+
+
+@pytest.mark.parametrize("E", [4, 8, 16])
+@pytest.mark.parametrize("n", [200_000, (1 << 20) + 999])   # the direct path, and the binned path
+def test_conflicting_duplicate_writes_keep_one_written_value(E, n):
+    # Writes whose duplicate indices carry different values: several results
+    # are correct (the paper does not order concurrent writes), so the test
+    # checks the validity rule -- every written element equals, bit for bit,
+    # one of the values written to its index (a torn or mixed record fails),
+    # and every other element is unchanged.
+    rng, g, o = grown_pair(E, 300 + E)
+    N = o.size()
+    before = as_records(dev_to_np(g.flatten(), E)[:N], E)
+    assert before.tobytes() == o.flatten().tobytes()
+    hot = rng.integers(0, N, size=4096, dtype=np.uint64)          # many writes per hot index
+    idx = np.where(rng.random(n) < 0.5, hot[rng.integers(0, hot.size, size=n)],
+                   rng.integers(0, N, size=n, dtype=np.uint64)).astype(np.uint64)
+    vals = wl.encode_values(wl.splitmix_at(4242 + E, np.arange(n, dtype=np.uint64)), E)   # distinct per write
+    if E == 16:   # make the two halves of a record disagree with every other write's halves
+        v = vals.view(np.uint64).reshape(-1, 2)
+        v[:, 1] = wl.splitmix_at(99, np.arange(n, dtype=np.uint64))
+    g.write(torch.from_numpy(idx.view(np.int64)).cuda(), values_to_dev(vals, E))
+    assert g.last_error() == gga.GGA_OK
+    after = as_records(dev_to_np(g.flatten(), E)[:N], E)
+    written = np.zeros(N, dtype=bool)
+    written[idx] = True
+    assert np.array_equal(after[~written], before[~written])
+    w = as_records(vals, E)
+    match = np.all(after[idx] == w, axis=1)                       # write i's value is the one kept
+    order = np.argsort(idx, kind="stable")
+    sidx = idx[order]
+    starts = np.flatnonzero(np.concatenate([[True], sidx[1:] != sidx[:-1]]))
+    kept_one = np.logical_or.reduceat(match[order], starts)
+    assert kept_one.all(), int((~kept_one).sum())
+    assert np.bincount(np.searchsorted(sidx[starts], idx), minlength=starts.size).max() > 8   # real conflicts
     g.close()
