@@ -59,7 +59,7 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=None,
                     help="steps of the end-to-end loop (default: --steps, as the device-timed loop)")
     ap.add_argument("--workload", choices=["paper_growth", "batched", "served", "two_phase", "doubling",
-                                           "insertion", "phases"],
+                                           "insertion", "phases", "random_access"],
                     default="paper_growth",
                     help="paper_growth: the headline step; batched: 4096 arrays in one persistent launch; "
                          "served: continuous-batching request server")
@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--n0", type=int, default=1 << 24, help="two_phase: initial records (a smaller case for profiling)")
     ap.add_argument("--generations", type=int, default=8, help="two_phase: spawning generations")
     ap.add_argument("--no-sweep", action="store_true", help="served: skip the arrival-rate sweep")
+    ap.add_argument("--l2-fetch", type=int, default=0,
+                    help="random_access: the context's L2 fetch granularity hint in bytes (0: leave the default)")
     ap.add_argument("--deadline", type=float, default=None,
                     help="served: seconds an append may wait for pool memory before it is rejected")
     return ap.parse_args()
@@ -90,7 +92,7 @@ KERNEL_SOURCES = {
     "wbin_scatter_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
     "wbin_apply_kernel": ["gga_access.cu", "gga_core.cuh", DEVICE_H],
 }
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_paper_growth_1024x512_B4096_R512.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_per_kernel_paper_growth_R96.md")
 
 
 def kernel_source_path(f: str) -> str:
@@ -108,15 +110,18 @@ def kernel_source_sha(kernel: str) -> str:
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` on the full workload from the
-    committed ncu summary, or None if absent or taken on other source."""
+def recorded_traffic(kernel: str, units: int):
+    """DRAM bytes of one launch of `kernel` over `units` work units (reads,
+    writes, elements or count rows, as the kernel's row of the committed
+    table says), from one-kernel ncu captures of the 96-round case scaled by
+    units / captured units; None if the kernel has no row or its source
+    changed since the capture."""
     try:
         for line in open(TRAFFIC_FILE):
             cells = [c.strip() for c in line.strip().strip("|").split("|")]
-            if len(cells) >= 5 and cells[0] == kernel and cells[4] == kernel_source_sha(kernel):
-                return int(cells[3])
-    except (OSError, ValueError):
+            if len(cells) >= 6 and cells[0] == kernel and cells[5] == kernel_source_sha(kernel):
+                return int(round(int(cells[4]) * units / int(cells[3])))
+    except (OSError, ValueError, ZeroDivisionError):
         pass
     return None
 
@@ -365,7 +370,8 @@ def run_ours(args, world, rank, local):
     for name in ("insert", "write"):
         phase_info[name]["kernels"] = kernels[name]
     ach = ab[dom] / (ph_ms[dom] / 1e3) / 1e9
-    traffic = recorded_traffic(kernels[dom]) if R == 512 and dom != "insert" else None
+    units = {"read": n_rand, "write": n_rand, "flatten": N, "rw_b": N, "rw_g": N}
+    traffic = recorded_traffic(kernels[dom], units[dom]) if dom in units else None
     roofline = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 3), "traffic": traffic, "kernel": kernels[dom], "phase": dom,
                 "algorithmic_bytes_per_launch": ab[dom],
@@ -833,6 +839,75 @@ def run_served(args, world, rank, local):
             "served": rep, "plain_one_launch_per_request": rep_plain, "load_sweep": sweep, "clocks": clocks}
 
 
+def set_l2_fetch_granularity(nbytes: int) -> int:
+    """The current context's cudaLimitMaxL2FetchGranularity (a hint of this
+    process's context, gone when it exits); returns the value in force."""
+    import ctypes
+    import glob
+    lib = ctypes.CDLL(sorted(glob.glob(os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64",
+                                                    "libcudart.so*")))[-1])
+    limit = 0x05   # cudaLimitMaxL2FetchGranularity
+    if nbytes:
+        assert lib.cudaDeviceSetLimit(limit, ctypes.c_size_t(nbytes)) == 0
+    v = ctypes.c_size_t(0)
+    assert lib.cudaDeviceGetLimit(ctypes.byref(v), limit) == 0
+    return int(v.value)
+
+
+def run_random_access(args, world, rank, local):
+    """The step's random reads alone, beside a flat gather of the same
+    indices: the paper-shaped array grown over --rounds rounds, 2^26 * R /
+    512 uniform indices (the density of the full step), gga_read against
+    torch.index_select on a flat copy.  For ncu captures of the two gathers
+    (DRAM bytes per access) and of the L2 fetch-granularity hint."""
+    from paper_2209_00103_gb300 import gga
+    from paper_2209_00103_gb300 import workloads as wl
+    dev = torch.device("cuda", local)
+    gran = set_l2_fetch_granularity(args.l2_fetch)
+    w = wl.paper_growth()
+    R = args.rounds
+    spec = wl.InsertSpec(L=w.L, T=w.T, E=w.E, seed=w.spec.seed, dist=w.spec.dist, rounds=R, coeffs=w.spec.coeffs)
+    counts, values = wl.make_insert_inputs_t(spec, dev)
+    N = int(values.shape[0])
+    n_rand = max(1, w.n_random * R // 512)
+    g = gga.GGArray(w.L, w.T, w.B, w.E, int(2.5 * N * w.E) + w.L * w.B * w.E * 4)
+    stream = torch.cuda.current_stream(dev)
+    g.insert(counts, values, stream)
+    del counts
+    idx = wl.uniform_indices_t(w.read_seed, n_rand, N, dev)
+    out = gga.elem_tensor(n_rand, w.E, dev)
+    del values
+    flat = g.flatten()[:N]
+    out_flat = torch.empty_like(out)
+
+    def timed(fn, k=max(3, args.steps)):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+    ms_g = timed(lambda: g.read(idx, out, stream))
+    ms_f = timed(lambda: torch.index_select(flat, 0, idx, out=out_flat))
+    assert torch.equal(out, out_flat)
+    g.close()
+    peak, _ = peaks()
+    alg = n_rand * (8 + 2 * w.E)
+    return {"metric": "random reads G accesses/s (GGArray gga_read vs flat index_select)",
+            "value": round(n_rand / (ms_g / 1e3) / 1e9, 3), "unit": "G accesses/s", "n_gpus": world,
+            "steps": max(3, args.steps), "warmup": max(3, args.warmup), "ms_per_step": round(ms_g, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"paper_growth_1024x512_B4096_int32_R{R}_random_reads", "elements": N,
+                       "reads": n_rand, "l2_fetch_granularity_bytes": gran},
+            "gga_read": {"ms": round(ms_g, 4), "achieved_gbs": round(alg / (ms_g / 1e3) / 1e9, 1),
+                         "frac_of_measured_peak": round(alg / (ms_g / 1e3) / 1e9 / peak, 3)},
+            "flat_index_select": {"ms": round(ms_f, 4)}, "gpu_launches": 2 * max(3, args.steps)}
+
+
 SWEEP_RATES = (20000.0, 50000.0, 100000.0, 200000.0, 500000.0, 1000000.0)
 SWEEP_P99_BOUND_MS = 10.0
 
@@ -1274,6 +1349,8 @@ def main():
         res = run_insertion(args, world, rank, local)
     elif args.workload == "phases":
         res = run_phases(args, world, rank, local)
+    elif args.workload == "random_access":
+        res = run_random_access(args, world, rank, local)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -8,19 +8,20 @@ import os
 import bench
 
 
-def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+def test_recorded_traffic_follows_the_source_hash_and_scales_by_units(tmp_path, monkeypatch):
     sha = bench.kernel_source_sha("read_kernel")
     assert len(sha) == 12
     f = tmp_path / "traffic.md"
-    f.write_text("| kernel | workload | launch | dram bytes | source |\n|---|---|---|---|---|\n"
-                 f"| read_kernel | w | l | 12345 | {sha} |\n"
-                 "| flatten_kernel | w | l | 999 | 000000000000 |\n")
+    f.write_text("| kernel | case | unit | units | dram bytes | source |\n|---|---|---|---|---|---|\n"
+                 f"| read_kernel | w | read | 1000 | 12345 | {sha} |\n"
+                 "| flatten_kernel | w | element | 10 | 999 | 000000000000 |\n")
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
-    assert bench.recorded_traffic("read_kernel") == 12345
-    assert bench.recorded_traffic("flatten_kernel") is None        # recorded on other source
-    assert bench.recorded_traffic("sweep_b_kernel") is None        # not recorded
+    assert bench.recorded_traffic("read_kernel", 1000) == 12345
+    assert bench.recorded_traffic("read_kernel", 4000) == 4 * 12345     # scaled by the units of the launch
+    assert bench.recorded_traffic("flatten_kernel", 10) is None         # recorded on other source
+    assert bench.recorded_traffic("sweep_b_kernel", 10) is None         # not recorded
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.md"))
-    assert bench.recorded_traffic("read_kernel") is None
+    assert bench.recorded_traffic("read_kernel", 1000) is None
 
 
 def test_every_kernel_with_sources_hashes_existing_files():
