@@ -793,7 +793,7 @@ def run_batched(args, world, rank, local):
            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "u32/u64/record", "data": "synthetic",
            "config": {"workload": f"batched_{len(sizes)}_lognormal_median64K_sigma1.5_cap16M", "arrays": len(sizes),
-                      "elements": total, "bytes": bytes_written, "rule": rule.__dict__,
+                      "elements": total, "bytes": bytes_written, "rule": rule.to_json() if hasattr(rule, "to_json") else rule.__dict__,
                       "step": "captured graph: clear every array + one persistent grow launch + fix-up + finalize"},
            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(gbs / peak, 3), "traffic": None, "kernel": "batch_grow_kernel",

@@ -65,11 +65,28 @@ def spec_for(gga_mod, a: int):
     return gga_mod.make_gen_spec((3 << 32) | a, "poisson", (0x10001, 0x9E3779B9, 7), round0=0, thresholds=thr)
 
 
-def build(sizes, rule: Rule, stream=None, pool_slack: float = 2.3):
+@dataclass
+class TypedRule:
+    """One Rule per payload size (4, 8 and 16 bytes)."""
+    by_payload: dict
+
+    def params_for(self, a: int, size: int):
+        return self.by_payload[payload_bytes(a)].params(size)
+
+    def to_json(self):
+        return {str(e): asdict(r) for e, r in self.by_payload.items()}
+
+
+def params_for(rule, a: int, size: int):
+    """(T, L, B) of array a of target `size` under a Rule or a TypedRule."""
+    return rule.params_for(a, size) if isinstance(rule, TypedRule) else rule.params(size)
+
+
+def build(sizes, rule, stream=None, pool_slack: float = 2.3):
     """Make the arrays (one shared pool) and the batch; returns
     (pool, arrays, batch, params list)."""
     from . import gga
-    params = [rule.params(int(s)) for s in sizes]
+    params = [params_for(rule, a, int(s)) for a, s in enumerate(sizes)]
     need = sum(int(s) * payload_bytes(a) for a, s in enumerate(sizes))
     first = sum(L * B * payload_bytes(a) for a, (_, L, B) in enumerate(params))
     pool_bytes = int(pool_slack * need + 2 * first + (256 << 20))
@@ -115,39 +132,80 @@ def memory_ratio(arrays) -> float:
 
 
 def candidates():
-    for T in (128, 256, 512, 1024):
-        for per_lfv in (8192, 32768, 131072):
-            for b_div in (4, 16):
+    """The global grid: blocks of 512 or 1024 threads (smaller ones measured
+    2-4x slower), 32K to 1M elements per LFVector, first bucket = the
+    LFVector's share / 1..16."""
+    for T in (512, 1024):
+        for per_lfv in (32768, 131072, 262144, 524288, 1048576):
+            for b_div in (1, 2, 4, 8, 16):
                 yield Rule(T=T, per_lfv=per_lfv, b_div=b_div)
 
 
+def neighbours(rule: Rule):
+    """Rules around `rule`: per_lfv and b_div halved, kept or doubled, both T."""
+    for T in (512, 1024):
+        for f in (0.5, 1, 2):
+            for d in (0.5, 1, 2):
+                per = int(rule.per_lfv * f)
+                bd = max(1, int(rule.b_div * d))
+                if 4096 <= per <= (4 << 20):
+                    yield Rule(T=T, per_lfv=per, b_div=bd)
+
+
 def autotune(sizes, stream, out_path: str = TUNED_FILE, max_ratio: float = 2.05, log=print):
-    """Measure every candidate rule on the GPU; keep the fastest whose memory
-    ratio is at most max_ratio.  Writes the choice and all measurements."""
+    """Measure candidate rules on the GPU and keep the fastest whose memory
+    ratio is at most max_ratio: first one rule for every array over the
+    global grid, then, payload type by payload type, the neighbours of the
+    best rule for that type's arrays with the others' rules fixed.  Writes
+    the choice and every measurement."""
     results = []
     total = int(np.sum(sizes))
-    for rule in candidates():
+
+    def measure(rule, tag):
         pool, arrays, batch, _ = build(sizes, rule, stream)
         ms = time_batch(batch, stream)
         ratio = memory_ratio(arrays)
         teardown(pool, arrays, batch)
-        rec = {"rule": asdict(rule), "ms": ms, "gelem_s": total / (ms / 1e3) / 1e9, "mem_ratio": ratio}
+        rec = {"stage": tag, "rule": rule.to_json() if isinstance(rule, TypedRule) else asdict(rule), "ms": ms,
+               "gelem_s": total / (ms / 1e3) / 1e9, "mem_ratio": ratio}
         results.append(rec)
         log(json.dumps(rec))
-    ok = [r for r in results if r["mem_ratio"] <= max_ratio] or results
-    best = min(ok, key=lambda r: r["ms"])
-    doc = {"chosen": best["rule"], "measured": results, "n_arrays": len(sizes), "elements": total,
+        return ms, ratio
+
+    best_rule, best_ms = None, math.inf
+    for rule in candidates():
+        ms, ratio = measure(rule, "global")
+        if ratio <= max_ratio and ms < best_ms:
+            best_rule, best_ms = rule, ms
+    if best_rule is None:
+        best_rule = Rule()
+    typed = TypedRule({4: best_rule, 8: best_rule, 16: best_rule})
+    for e in (4, 8, 16):
+        for cand in neighbours(typed.by_payload[e]):
+            if cand == typed.by_payload[e]:
+                continue
+            trial = TypedRule(dict(typed.by_payload))
+            trial.by_payload[e] = cand
+            ms, ratio = measure(trial, f"payload{e}")
+            if ratio <= max_ratio and ms < best_ms:
+                typed, best_ms = trial, ms
+    doc = {"chosen_by_payload": typed.to_json(), "ms": best_ms, "measured": results, "n_arrays": len(sizes),
+           "elements": total, "max_mem_ratio": max_ratio,
            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())}
     with open(out_path, "w") as f:
         json.dump(doc, f, indent=1)
-    return Rule(**best["rule"])
+    return typed
 
 
-def tuned_rule() -> Rule:
-    """The rule the autotuner chose, or the default rule."""
+def tuned_rule():
+    """The rule the autotuner chose (per payload type when it chose so), or
+    the default rule."""
     try:
         with open(TUNED_FILE) as f:
-            return Rule(**json.load(f)["chosen"])
+            doc = json.load(f)
+        if "chosen_by_payload" in doc:
+            return TypedRule({int(e): Rule(**r) for e, r in doc["chosen_by_payload"].items()})
+        return Rule(**doc["chosen"])
     except (OSError, KeyError, ValueError, TypeError):
         return Rule()
 

@@ -251,7 +251,21 @@ struct GenShared {
   uint32_t commit, nb;
   int stop;                   // 1: pool exhausted, 2: target reached
   uint64_t tab[kMaxBuckets];  // the LFVector's bucket table (copy)
+  // Threshold counts (ascending thresholds): ptab[i] = #{k : thr[k] <= i * 2^24},
+  // so a draw u in [i * 2^24, (i + 1) * 2^24) counts ptab[i] plus the few
+  // thresholds inside its interval.
+  uint32_t thr[GGA_MAX_THRESHOLDS];
+  uint8_t ptab[256];
 };
+
+// Count of draw u (the high word) against ascending thresholds through the
+// table: start from the thresholds below u's interval of 2^24, then step
+// over those inside it.  Equal to #{k < nthr : u >= thr[k]}.
+__device__ __forceinline__ uint32_t table_count(const GenShared& sh, uint32_t nthr, uint32_t u) {
+  uint32_t c = sh.ptab[u >> 24];
+  while (c < nthr && u >= sh.thr[c]) ++c;
+  return c;
+}
 
 // Returns the number of rounds it drew; *done is set when the LFVector
 // reached `target` or the pool ran out.  Every thread of the block calls
@@ -281,6 +295,15 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
     const uint32_t nb0 = v.nbuckets[l];
     for (uint32_t i = t0; i < nb0; i += NT) sh.tab[i] = bk[i];
   }
+  const bool tabled = DIST == GGA_DIST_POISSON && g.thr_sorted;   // uniform
+  if (tabled) {
+    for (uint32_t i = t0; i < GGA_MAX_THRESHOLDS; i += NT) sh.thr[i] = g.thr[i];
+    for (uint32_t i = t0; i < 256; i += NT) {
+      uint32_t c = 0;
+      for (uint32_t k = 0; k < g.nthr; ++k) c += g.thr[k] <= (i << 24) ? 1u : 0u;
+      sh.ptab[i] = static_cast<uint8_t>(c);
+    }
+  }
   __syncthreads();
   uint32_t r0 = 0;
   while (r0 < R && sh.stop == 0) {
@@ -302,8 +325,13 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
         uint32_t c0 = 0, c1 = 0;
         if (k < kk) {
-          if (tfirst < v.T) c0 = gen_count_state<SEARCH, DIST>(g, d0.state(r));
-          if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = gen_count_state<SEARCH, DIST>(g, d1.state(r));
+          if (DIST == GGA_DIST_POISSON && tabled) {
+            if (tfirst < v.T) c0 = table_count(sh, g.nthr, splitmix_mix_hi(d0.state(r)));
+            if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = table_count(sh, g.nthr, splitmix_mix_hi(d1.state(r)));
+          } else {
+            if (tfirst < v.T) c0 = gen_count_state<SEARCH, DIST>(g, d0.state(r));
+            if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = gen_count_state<SEARCH, DIST>(g, d1.state(r));
+          }
         }
         if (KV > 1) c0w[KV > 1 ? k / 4 : 0] |= c0 << (8 * (k % 4));
         c[h] = c0 + c1;
