@@ -647,7 +647,7 @@ def time_generated(w, R, pool_bytes, dev, stream, per_round=False):
 
 def time_push_expand(spec, B, counts, pool_bytes, dev, stream):
     """Pushes of values read from device memory through the device API
-    (gga_push_expand: gga::block_push_rounds, 8 rounds per call): the same
+    (gga_push_expand: gga::block_push_rounds, 4 rounds per call): the same
     counts as the step's insertion, and one int32 input per (round, block,
     thread) that the thread appends `count` times.  Algorithmic bytes: the
     counts and inputs read (4 + E per thread and round) and E per element
@@ -681,7 +681,7 @@ def time_push_expand(spec, B, counts, pool_bytes, dev, stream):
             "frac_of_8tbs": round(gbs / 8000.0, 3), "device_error": rc,
             "kernels": "push_expand_kernel + finalize_kernel",
             "note": "counts [R][L][T] and one input per (round, block, thread) read from HBM; "
-                    "block_push_rounds of 8 rounds, staged 128-bit stores"}
+                    "block_push_rounds of 4 rounds, 4 slots per thread, staged 128-bit stores"}
 
 
 # ---------------------------------------------------------------------------

@@ -251,9 +251,10 @@ int gga_insert_generated(gga_handle h, const gga_gen_spec* spec, uint32_t rounds
  *  is assembled in shared memory and written with 128-bit stores.
  *
  * gga_push_expand -- pushes of values read from device memory, written as a
- *  user kernel of the device API (one block of T <= 512 threads per
- *  LFVector; gga::block_push_rounds, 8 rounds per call for 4-byte
- *  elements, 4 for 8-byte, 2 for 16-byte), then gga_device_commit.  In
+ *  user kernel of the device API (one block per LFVector of T <= 512 slots,
+ *  each thread playing 4 consecutive slots -- 2 for 16-byte elements --;
+ *  gga::block_push_rounds, 4 rounds per call for 4-byte elements, 2 for
+ *  8- and 16-byte), then gga_device_commit.  In
  *  round r, thread t of block l appends counts_dev[r][l][t] copies of
  *  inputs_dev[r][l][t].  counts_dev: device, uint32 [rounds][L][T], 4-byte
  *  aligned; inputs_dev: device, E-byte elements [rounds][L][T], E-byte

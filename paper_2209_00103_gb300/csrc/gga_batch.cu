@@ -24,7 +24,14 @@ int launch_clear(const ArrayView& v, cudaStream_t st);
 
 namespace {
 
-constexpr int kBatchThreads = 512;        // up to 2 virtual threads per thread (T <= 1024)
+// Threads per block and virtual threads per thread (T <= kBatchThreads *
+// kBatchKV = 1024) and resident blocks per SM.
+#ifndef GGA_BATCH_THREADS
+#define GGA_BATCH_THREADS 512
+#endif
+constexpr int kBatchThreads = GGA_BATCH_THREADS;
+constexpr int kBatchKV = 1024 / kBatchThreads;
+constexpr int kBatchMinBlocks = 1024 / kBatchThreads;
 constexpr uint32_t kBatchStageBytes = 49152;
 constexpr uint32_t kBatchMaxRounds = 1u << 20;
 
@@ -42,6 +49,29 @@ struct BatchItem {
 // Grow LFVector l of job J to its share of the target: rounds of in-thread
 // insertions in passes of K (grow_passes in gga_gen.cuh), clipped at the
 // target.  All threads of the block call it.
+#ifndef GGA_BATCH_NOINLINE
+#define GGA_BATCH_NOINLINE 0
+#endif
+// One distribution's pass loop; with GGA_BATCH_NOINLINE a function of its
+// own, register-allocated apart from the other (payload, distribution) forms.
+template <int E, int K, int DIST>
+__device__ __forceinline__ uint32_t grow_item_passes_inl(const ArrayView& v, const GenParams& g, uint32_t l,
+                                                         uint64_t target, GenShared& sh, uint4* stage, bool* done) {
+  return grow_passes<E, K, kBatchKV, true, DIST>(v, g, l, kBatchMaxRounds, target, sh, stage, kBatchStageBytes / E,
+                                                 done);
+}
+template <int E, int K, int DIST>
+__device__ __noinline__ uint32_t grow_item_passes_call(const ArrayView& v, const GenParams& g, uint32_t l,
+                                                       uint64_t target, GenShared& sh, uint4* stage, bool* done) {
+  return grow_item_passes_inl<E, K, DIST>(v, g, l, target, sh, stage, done);
+}
+template <int E, int K, int DIST>
+__device__ __forceinline__ uint32_t grow_item_passes(const ArrayView& v, const GenParams& g, uint32_t l,
+                                                     uint64_t target, GenShared& sh, uint4* stage, bool* done) {
+  return GGA_BATCH_NOINLINE ? grow_item_passes_call<E, K, DIST>(v, g, l, target, sh, stage, done)
+                            : grow_item_passes_inl<E, K, DIST>(v, g, l, target, sh, stage, done);
+}
+
 template <int E>
 __device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* stage) {
   const ArrayView& v = J.v;
@@ -54,27 +84,23 @@ __device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* s
   // One dispatch per item on the count distribution, none per draw.
   switch (J.g.dist) {
     case GGA_DIST_BERNOULLI:
-      drawn = grow_passes<E, K, 2, true, GGA_DIST_BERNOULLI>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
-                                                             kBatchStageBytes / E, &done);
+      drawn = grow_item_passes<E, K, GGA_DIST_BERNOULLI>(v, J.g, l, target, sh, stage, &done);
       break;
     case GGA_DIST_UNIFORM3:
-      drawn = grow_passes<E, K, 2, true, GGA_DIST_UNIFORM3>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
-                                                            kBatchStageBytes / E, &done);
+      drawn = grow_item_passes<E, K, GGA_DIST_UNIFORM3>(v, J.g, l, target, sh, stage, &done);
       break;
     case GGA_DIST_GEOMETRIC:
-      drawn = grow_passes<E, K, 2, true, GGA_DIST_GEOMETRIC>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
-                                                             kBatchStageBytes / E, &done);
+      drawn = grow_item_passes<E, K, GGA_DIST_GEOMETRIC>(v, J.g, l, target, sh, stage, &done);
       break;
     default:
-      drawn = grow_passes<E, K, 2, true, GGA_DIST_POISSON>(v, J.g, l, kBatchMaxRounds, target, sh, stage,
-                                                           kBatchStageBytes / E, &done);
+      drawn = grow_item_passes<E, K, GGA_DIST_POISSON>(v, J.g, l, target, sh, stage, &done);
       break;
   }
   if (threadIdx.x == 0 && !done && drawn >= kBatchMaxRounds) latch_error(v.status, GGA_ERR_TIMEOUT);
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) batch_grow_kernel(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks) batch_grow_kernel(const BatchJob* __restrict__ jobs,
                                                                       const BatchItem* __restrict__ items,
                                                                       uint32_t n_items, uint32_t* ticket) {
   extern __shared__ uint4 s_stage4[];

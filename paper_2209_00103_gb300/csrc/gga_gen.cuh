@@ -51,6 +51,7 @@ __device__ __forceinline__ uint64_t splitmix(uint64_t seed, uint64_t key) {
 struct RoundDraws {
   uint64_t base;   // seed + (gl + 1) * GOLDEN
   uint32_t gh;     // gid >> 32
+  __device__ __forceinline__ RoundDraws() : base(0), gh(0) {}
   __device__ __forceinline__ RoundDraws(uint64_t seed, uint64_t gid)
       : base(seed + ((gid & 0xFFFFFFFFull) + 1ull) * kGolden), gh(static_cast<uint32_t>(gid >> 32)) {}
   __device__ __forceinline__ uint64_t state(uint64_t round) const {
@@ -214,9 +215,9 @@ __device__ inline void finalize_block(const ArrayView& v, const uint64_t* ins_ba
 // block per item, rounds until the LFVector's target).
 //
 // Per pass every thread draws its counts for K rounds (virtual threads
-// t = t0 * kv + i, kv = ceil(T / blockDim) <= KV), the per-thread round sums
-// are scanned two rounds per 32-bit word (sums < 2^16 per block: counts are
-// below 64 and blockDim * kv <= 1024), warp 0 scans the warp totals and its
+// t = t0 * kv + i, kv = ceil(T / blockDim) <= KV <= 4), the per-thread round
+// sums are scanned two rounds per 32-bit word (sums < 2^16 per block: counts
+// are below 64 and blockDim * KV * 63 < 2^16), warp 0 scans the warp totals and its
 // lane 0 makes one size reservation for the pass -- clipped at `target`,
 // and, if the pool cannot hold the buckets it reaches, cut back to the
 // longest prefix of whole rounds that fits -- and takes the buckets
@@ -285,7 +286,9 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
   const uint64_t tfirst = static_cast<uint64_t>(t0) * kv;        // first virtual thread
   const uint64_t gfirst = static_cast<uint64_t>(l) * v.T + tfirst;
   const uint64_t* bk = v.buckets + static_cast<uint64_t>(l) * kMaxBuckets;
-  const RoundDraws d0(g.seed, gfirst), d1(g.seed, gfirst + 1);   // virtual threads gfirst, gfirst + 1
+  RoundDraws dv[KV];   // virtual threads gfirst, ..., gfirst + KV - 1
+#pragma unroll
+  for (int i = 0; i < KV; ++i) dv[i] = RoundDraws(g.seed, gfirst + i);
   if (t0 == 0) {
     sh.base = v.sizes[l];
     sh.nb = v.nbuckets[l];
@@ -308,14 +311,15 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
   uint32_t r0 = 0;
   while (r0 < R && sh.stop == 0) {
     const uint32_t kk = min(static_cast<uint32_t>(K), R - r0);
-    // pk: the thread's per-round sums, two rounds per word.  c0w: with two
-    // virtual threads, the first one's count of round k in byte k % 4 of
-    // word k / 4 (the second's is the sum minus it); with one, the count is
-    // pk's half-word.
-    constexpr int KC = KV > 1 ? (K + 3) / 4 : 1;
-    uint32_t pk[KP], inc[KP], c0w[KC];
+    // pk: the thread's per-round sums, two rounds per word.  cw: with KV
+    // virtual threads, the counts of the first KV - 1 of them, one byte
+    // each (round k, virtual thread i at byte k * (KV - 1) + i; the last
+    // one's count is the sum minus theirs); with one, the count is pk's
+    // half-word.
+    constexpr int KC = KV > 1 ? (K * (KV - 1) + 3) / 4 : 1;
+    uint32_t pk[KP], inc[KP], cw[KC];
 #pragma unroll
-    for (int q = 0; q < KC; ++q) c0w[q] = 0;
+    for (int q = 0; q < KC; ++q) cw[q] = 0;
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       uint32_t c[2];
@@ -323,18 +327,21 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
       for (int h = 0; h < 2; ++h) {
         const uint32_t k = 2 * j + h;
         const uint64_t r = static_cast<uint64_t>(g.round0) + r0 + k;
-        uint32_t c0 = 0, c1 = 0;
-        if (k < kk) {
-          if (DIST == GGA_DIST_POISSON && tabled) {
-            if (tfirst < v.T) c0 = table_count(sh, g.nthr, splitmix_mix_hi(d0.state(r)));
-            if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = table_count(sh, g.nthr, splitmix_mix_hi(d1.state(r)));
-          } else {
-            if (tfirst < v.T) c0 = gen_count_state<SEARCH, DIST>(g, d0.state(r));
-            if (KV > 1 && kv > 1 && tfirst + 1 < v.T) c1 = gen_count_state<SEARCH, DIST>(g, d1.state(r));
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < KV; ++i) {
+          uint32_t ci = 0;
+          if (k < kk && (KV == 1 || static_cast<uint32_t>(i) < kv) && tfirst + i < v.T) {
+            if (DIST == GGA_DIST_POISSON && tabled) ci = table_count(sh, g.nthr, splitmix_mix_hi(dv[i].state(r)));
+            else ci = gen_count_state<SEARCH, DIST>(g, dv[i].state(r));
           }
+          if (KV > 1 && i < KV - 1) {
+            const int q = static_cast<int>(k) * (KV - 1) + i;
+            cw[KV > 1 ? q / 4 : 0] |= ci << (8 * (q % 4));
+          }
+          sum += ci;
         }
-        if (KV > 1) c0w[KV > 1 ? k / 4 : 0] |= c0 << (8 * (k % 4));
-        c[h] = c0 + c1;
+        c[h] = sum;
       }
       pk[j] = c[0] | (c[1] << 16);
       inc[j] = warp_incl_scan_u32(pk[j]);
@@ -406,11 +413,16 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
       for (int h = 0; h < 2; ++h) {
         const uint32_t k = 2 * j + h;
         uint32_t st = sh.rb[k] + ((ex >> (16 * h)) & 0xFFFFu);
+        const uint32_t csum = (pk[j] >> (16 * h)) & 0xFFFFu;
+        uint32_t before = 0;   // elements of the earlier virtual threads of this round
 #pragma unroll
         for (int i = 0; i < KV; ++i) {
-          const uint32_t csum = (pk[j] >> (16 * h)) & 0xFFFFu;
-          const uint32_t cfirst = KV > 1 ? (c0w[KV > 1 ? k / 4 : 0] >> (8 * (k % 4))) & 0xFFu : csum;
-          const uint32_t c = i == 0 ? cfirst : csum - cfirst;
+          uint32_t c = csum - before;
+          if (KV > 1 && i < KV - 1) {
+            const int q = static_cast<int>(k) * (KV - 1) + i;
+            c = (cw[KV > 1 ? q / 4 : 0] >> (8 * (q % 4))) & 0xFFu;
+          }
+          before += c;
           V val = vr + static_cast<V>(g.va) * static_cast<V>(i) + static_cast<V>(g.vb) * static_cast<V>(k);
           if (whole && DIST >= 0 && max_count<DIST>() > 0 && max_count<DIST>() <= 2) {
             // At most two elements: predicated stores, no loop.

@@ -798,24 +798,25 @@ int launch_finalize(const ArrayView& v, cudaStream_t st) {
 
 // A pass's values are staged in shared memory (a pass averages 16 KB at
 // K = 8 rounds, 512 threads, one int32 per thread and round; a pass that
-// does not fit writes directly).  Blocks of up to 512 threads are compiled
-// for 3 resident per SM (40 registers) with a 48 KB stage: measured on
-// GB300 for 1024 blocks x 512 threads x 512 rounds, 1.29 ms against 1.43 ms
-// with 64 KB and the default register budget (2 resident), and 1.35 ms at
-// 4 (spills).  GGA_GEN_VT = 1 plays T in (256, 512] with half as many
-// threads, two virtual threads each (one scan word covers both), and
-// GGA_GEN_MINB_VT resident blocks with a 32 KB stage.
+// does not fit writes directly).  T in (256, 512] is played by blocks of
+// T / GGA_GEN_VT threads, GGA_GEN_VT virtual threads each (one scan word
+// and one share of every barrier serve them), GGA_GEN_MINB_VT resident per
+// SM with a GGA_GEN_STAGE_VT-byte stage: measured on GB300 for the
+// paper-shaped workload (1024 LFVectors x 512 threads x 512 rounds, int32),
+// 128 threads x 4, 8 per SM: 0.737 ms; 256 x 2, 4 per SM: 0.753 ms; 512 x 1,
+// 3 per SM (40 registers, 48 KB stage): 0.816 ms.  Other T use one virtual
+// thread per thread, blocks of up to 512 threads 3 per SM (up to 1024: 1).
 #ifndef GGA_GEN_VT
-#define GGA_GEN_VT 0
+#define GGA_GEN_VT 4
 #endif
 #ifndef GGA_GEN_MINB_VT
-#define GGA_GEN_MINB_VT 6
+#define GGA_GEN_MINB_VT 8
 #endif
 #ifndef GGA_GEN_MINB512
 #define GGA_GEN_MINB512 3
 #endif
 #ifndef GGA_GEN_STAGE_VT
-#define GGA_GEN_STAGE_VT 32768
+#define GGA_GEN_STAGE_VT 24576
 #endif
 constexpr uint32_t kGenStageBytes = 49152;
 constexpr uint32_t kGenStageBytesVT = GGA_GEN_STAGE_VT;
@@ -837,8 +838,8 @@ __global__ void __launch_bounds__(MAXT, MINB) gen_insert_kernel(const __grid_con
 int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32_t R, uint32_t* /*done*/,
                             int /*num_sms*/, cudaStream_t st) {
   const GenParams g = make_gen_params(spec);
-  const bool vt = GGA_GEN_VT && v.T > 256 && v.T <= 512;
-  const uint32_t NT = vt ? ((v.T + 1) / 2 + 31) / 32 * 32 : (v.T + 31) / 32 * 32;
+  const bool vt = GGA_GEN_VT > 1 && v.T > 256 && v.T <= 512;
+  const uint32_t NT = vt ? ((v.T + GGA_GEN_VT - 1) / GGA_GEN_VT + 31) / 32 * 32 : (v.T + 31) / 32 * 32;
   const size_t smem = vt ? kGenStageBytesVT : kGenStageBytes;
 #define GGA_GEN_AD(EE, KK, KV, MT, MB, DD)                                                                   \
   do {                                                                                                       \
@@ -861,7 +862,8 @@ int launch_insert_generated(const ArrayView& v, const gga_gen_spec& spec, uint32
   // and round (K halves for blocks of more than 512 threads beyond 4 bytes).
 #define GGA_GEN(EE)                                                                                          \
   do {                                                                                                       \
-    if (vt) GGA_GEN_AS(EE, GenK<EE>::value, 2, 256, GGA_GEN_MINB_VT);                                        \
+    if (vt) GGA_GEN_AS(EE, GenK<EE>::value, (GGA_GEN_VT > 1 ? GGA_GEN_VT : 2), 512 / (GGA_GEN_VT > 1 ? GGA_GEN_VT : 2),   \
+                       GGA_GEN_MINB_VT);                                                                     \
     else if (NT <= 512) GGA_GEN_AS(EE, GenK<EE>::value, 1, 512, GGA_GEN_MINB512);                            \
     else GGA_GEN_AS(EE, (EE == 4 ? 8 : GenK<EE>::value / 2), 1, 1024, 1);                                    \
   } while (0)

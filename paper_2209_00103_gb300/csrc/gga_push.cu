@@ -20,11 +20,6 @@ namespace gga {
 // per round through a BlockPusher on LFVector l.  A round that does not fit
 // ends the block's rounds (the rounds that fit are kept, as in every
 // insertion).
-// Stage of one block_push_rounds call of the memory-sourced pushes: K = 8
-// rounds of 512 threads average 16 KB of int32 at one element per thread
-// and round.
-constexpr uint32_t kExpandStageBytes = 32768;
-
 template <int E>
 __global__ void __launch_bounds__(1024) push_generated_kernel(const ArrayView* view, GenParams g, uint32_t R) {
   typedef typename Elem<E>::T T;
@@ -52,69 +47,88 @@ int launch_push_generated(const ArrayView& v, const ArrayView* dview, const gga_
   return launch_finalize(v, st);
 }
 
-// Memory-sourced pushes through the device API: block l reads, for K
-// rounds at a time, its threads' counts counts[r][l][t] and inputs
-// inputs[r][l][t] (coalesced, all 2K loads of a thread issued before any is
-// used) and appends, per thread and round, `count` copies of its input with
-// one block_push_rounds call for the K rounds (staged, 128-bit stores).  A
-// call that does not fit ends the block's rounds.
-// Two resident blocks of 512 threads per SM: the 2K loads of a pass are
-// then held in registers until used (with 40 registers they spill, and a
-// spilled load is waited for at once, which serialises them).
-#ifndef GGA_EXPAND_MINB
-#define GGA_EXPAND_MINB 2
-#endif
-template <int E, int K>
-__global__ void __launch_bounds__(512, GGA_EXPAND_MINB) push_expand_kernel(const ArrayView* view,
-                                                             const uint32_t* __restrict__ counts,
-                                                             const typename Elem<E>::T* __restrict__ inputs,
-                                                             uint32_t R, uint32_t L, uint32_t T,
-                                                             uint32_t stage_bytes) {
+// Memory-sourced pushes through the device API: block l appends, per
+// thread slot t and round r, counts[r][l][t] copies of inputs[r][l][t],
+// K rounds per gga::block_push_rounds call (staged, 128-bit stores).  A
+// thread plays S consecutive slots S t, ..., S t + S - 1 and pushes their
+// counts together (its elements are slot S t's copies, then S t + 1's, ...,
+// which is their order in the LFVector): one scan slot and one share of
+// every barrier then serve S slots, and the blocks (512 / S threads for
+// T = 512) are small enough for all 1024 of the paper-shaped workload to
+// be resident at once.  Each thread loads its 2 K S counts and inputs of a
+// call before using any.  A call that does not fit ends the block's rounds.
+// Measured on GB300 for the paper-shaped workload (1024 x 512, 512 rounds,
+// int32): one slot per thread, K = 8, 2 blocks per SM: 1.42 ms (with the
+// loads prefetched into shared memory by cp.async: 1.52 ms); S = 2, K = 4,
+// 4 per SM: 0.98 ms; S = 4, K = 2, 8 per SM: 0.90 ms; S = 4, K = 4, 8 per
+// SM: 0.84 ms.
+template <int E, int K, int S, int MINB>
+__global__ void __launch_bounds__(512 / S, MINB) push_expand_s_kernel(const ArrayView* view,
+                                                                  const uint32_t* __restrict__ counts,
+                                                                  const typename Elem<E>::T* __restrict__ inputs,
+                                                                  uint32_t R, uint32_t L, uint32_t T,
+                                                                  uint32_t stage_bytes) {
   typedef typename Elem<E>::T V;
   extern __shared__ uint4 s_stage[];
-  const uint32_t l = blockIdx.x, t = threadIdx.x;
-  // (A bulk L2 prefetch of the next pass's rows by thread 0 measured slower:
-  // 1.51 ms against 1.37 ms for the paper-shaped workload.)
+  const uint32_t l = blockIdx.x, t = S * threadIdx.x;
 #pragma unroll 1
   for (uint32_t r0 = 0; r0 < R; r0 += K) {
-    uint32_t c[K];
-    V x[K];
+    uint32_t c[K], cs[K][S];
+    V x[K][S];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const uint32_t r = r0 + k;
       c[k] = 0;
-      x[k] = V();
-      if (r < R && t < T) {
-        const uint64_t i = (static_cast<uint64_t>(r) * L + l) * T + t;
-        c[k] = __ldcs(counts + i);
-        x[k] = __ldcs(inputs + i);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        cs[k][i] = 0;
+        x[k][i] = V();
+        if (r < R && t + i < T) {
+          const uint64_t at = (static_cast<uint64_t>(r) * L + l) * T + t + i;
+          cs[k][i] = __ldcs(counts + at);
+          x[k][i] = __ldcs(inputs + at);
+        }
+        c[k] += cs[k][i];
       }
     }
-    const uint32_t done =
-        block_push_rounds<V, K>(view, l, c, [&](uint32_t kr, uint32_t) { return x[kr]; }, s_stage, stage_bytes);
+    const uint32_t done = block_push_rounds<V, K>(
+        view, l, c,
+        [&](uint32_t kr, uint32_t m) {
+          V v = x[kr][S - 1];
+#pragma unroll
+          for (int i = S - 2; i >= 0; --i) {
+            uint32_t before = 0;
+#pragma unroll
+            for (int j = 0; j <= i; ++j) before += cs[kr][j];
+            if (m < before) v = x[kr][i];
+          }
+          return v;
+        },
+        s_stage, stage_bytes);
     if (done < static_cast<uint32_t>(K)) break;
   }
 }
 
-int launch_push_expand(const ArrayView& v, const ArrayView* dview, const uint32_t* counts, const void* inputs,
-                       uint32_t rounds, cudaStream_t st) {
-  const uint32_t NT = (v.T + 31) / 32 * 32;
-  if (NT > 512) return GGA_ERR_INVALID;
-  const size_t smem = kExpandStageBytes;
-#define GGA_EXPAND(EE, KK)                                                                                     \
-  do {                                                                                                         \
-    cudaFuncSetAttribute(push_expand_kernel<EE, KK>, cudaFuncAttributeMaxDynamicSharedMemorySize,             \
-                         static_cast<int>(smem));                                                              \
-    push_expand_kernel<EE, KK><<<v.L, NT, smem, st>>>(                                                         \
-        dview, counts, static_cast<const typename Elem<EE>::T*>(inputs), rounds, v.L, v.T,                     \
-        static_cast<uint32_t>(smem));                                                                          \
-  } while (0)
-  if (v.E == 4) GGA_EXPAND(4, 8);
-  else if (v.E == 8) GGA_EXPAND(8, 4);
-  else GGA_EXPAND(16, 2);
-#undef GGA_EXPAND
+template <int E, int K, int S, int MINB>
+int launch_expand_s(const ArrayView& v, const ArrayView* dview, const uint32_t* counts, const void* inputs,
+                    uint32_t rounds, cudaStream_t st) {
+  const uint32_t NTS = ((v.T + S - 1) / S + 31) / 32 * 32;
+  // Stage: twice a call's elements at one per slot of 512 (larger calls go unstaged).
+  const size_t smem = static_cast<size_t>(K) * 512u * E * 2u;
+  auto kern = push_expand_s_kernel<E, K, S, MINB>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  kern<<<v.L, NTS, smem, st>>>(dview, counts, static_cast<const typename Elem<E>::T*>(inputs), rounds, v.L, v.T,
+                               static_cast<uint32_t>(smem));
   if (cudaGetLastError() != cudaSuccess) return GGA_ERR_CUDA;
   return launch_finalize(v, st);
+}
+
+int launch_push_expand(const ArrayView& v, const ArrayView* dview, const uint32_t* counts, const void* inputs,
+                       uint32_t rounds, cudaStream_t st) {
+  if (v.T > 512) return GGA_ERR_INVALID;
+  if (v.E == 4) return launch_expand_s<4, 4, 4, 8>(v, dview, counts, inputs, rounds, st);
+  if (v.E == 8) return launch_expand_s<8, 2, 4, 8>(v, dview, counts, inputs, rounds, st);
+  return launch_expand_s<16, 2, 2, 4>(v, dview, counts, inputs, rounds, st);
 }
 
 }  // namespace gga
