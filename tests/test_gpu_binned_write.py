@@ -97,3 +97,26 @@ def test_conflicting_duplicate_writes_keep_one_written_value(E, n):
     assert kept_one.all(), int((~kept_one).sum())
     assert np.bincount(np.searchsorted(sidx[starts], idx), minlength=starts.size).max() > 8   # real conflicts
     g.close()
+
+
+def test_binned_writes_on_an_array_of_more_than_2_gb():
+    # 16-byte elements, ~141M of them (2.26 GB): 256 bins of 8 MB no longer
+    # cover the array, so the bins are widened (the shift is raised) -- the
+    # branch the 1 GB workloads never take.
+    L, T, B, E, R = 512, 512, 4096, 16, 540
+    coeffs = (10, 1 << 20, 1)
+    g = gga.GGArray(L, T, B, E, 5 << 30)
+    o = oracle.OracleGGArray(L, T, B, E)
+    g.insert_generated(gga.make_gen_spec(17, "uniform3", coeffs), R)
+    o.insert_generated(17, "uniform3", coeffs, 0, R)
+    N = o.size()
+    assert N * E > (256 << 23)
+    rng = np.random.default_rng(21)
+    idx = rng.integers(0, N, size=(1 << 21) + 5, dtype=np.uint64)
+    vals = wl.index_keyed_values(77, idx, E)
+    g.write(torch.from_numpy(idx.view(np.int64)).cuda(), values_to_dev(vals, E))
+    assert o.write(idx, vals) == oracle.OK
+    assert g.last_error() == gga.GGA_OK
+    assert_same_state(g, o)
+    g.close()
+    o.close()
