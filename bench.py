@@ -591,6 +591,24 @@ def run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world,
     for k in range(2):
         step(k)
     torch.cuda.synchronize(dev)
+
+    def copy_gbs(dst, src, s, reps=3):
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            with torch.cuda.stream(s):
+                dst.copy_(src, non_blocking=True)
+            e1.record(s)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return src.numel() * src.element_size() / (best / 1e3) / 1e9
+
+    # The host link alone, on the largest input and output of the step: the
+    # step cannot run faster than its uploads at this rate.
+    h2d_gbs = copy_gbs(dev_in[1][1], host_in[1], up)
+    d2h_gbs = copy_gbs(host_out[1], dev_out[1][1], down)
     barrier(world)
     K = args.e2e_steps if args.e2e_steps is not None else args.steps
     a = torch.cuda.Event(enable_timing=True)
@@ -608,9 +626,14 @@ def run_e2e(args, g, counts, values, idx_r, idx_w, vals_w, out_r, dst, N, world,
     for t in dev_in:
         del t[1]
     del dev_out[0][1], dev_out[1][1]
+    bound_ms = h2d / (h2d_gbs * 1e9) * 1e3
     return {"value": round(total / (ms / 1e3) / 1e9, 3), "unit": "Gelem/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms / K, 3), "steps": K,
-            "pipelining": "double-buffered inputs/outputs, uploads and downloads on their own streams"}
+            "pipelining": "double-buffered inputs/outputs, uploads and downloads on their own streams",
+            "host_link": {"h2d_gbs": round(h2d_gbs, 1), "d2h_gbs": round(d2h_gbs, 1),
+                          "h2d_bound_ms_per_step": round(bound_ms, 3), "frac": round(bound_ms / (ms / K), 3),
+                          "note": "pinned copies of the step's values (h2d) and flattened array (d2h) alone, "
+                                  "CUDA events; the bound is the step's uploads at the h2d rate"}}
 
 
 def time_generated(w, R, pool_bytes, dev, stream, per_round=False):
