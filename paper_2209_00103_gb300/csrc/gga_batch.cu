@@ -32,7 +32,11 @@ namespace {
 constexpr int kBatchThreads = GGA_BATCH_THREADS;
 constexpr int kBatchKV = 1024 / kBatchThreads;
 constexpr int kBatchMinBlocks = 1024 / kBatchThreads;
-constexpr uint32_t kBatchStageBytes = 49152;
+// Stage of a pass: 80 KB, two blocks per SM.  Measured on GB300 for the
+// 4096-array workload (rounds per pass for 8- / 16-byte payloads): 48 KB
+// with 4 / 2 rounds 4.30 ms, 80 KB with 4 / 4 rounds 4.24 ms, 96 KB with
+// 4 / 4 4.25 ms, with 6 / 4 4.31 ms.
+constexpr uint32_t kBatchStageBytes = 81920;
 constexpr uint32_t kBatchMaxRounds = 1u << 20;
 
 struct BatchJob {
@@ -77,8 +81,8 @@ __device__ void grow_item(const BatchJob& J, uint32_t l, GenShared& sh, uint4* s
   const ArrayView& v = J.v;
   const uint64_t target = J.target / v.L + (l < J.target % v.L ? 1 : 0);
   // Rounds per pass: a pass of T <= 1024 threads at one element per thread
-  // and round then averages <= 32 KB, inside the 48 KB stage.
-  constexpr int K = E == 4 ? 8 : (E == 8 ? 4 : 2);
+  // and round then averages <= 64 KB, inside the 80 KB stage.
+  constexpr int K = E == 4 ? 8 : 4;
   uint32_t drawn;
   bool done;
   // One dispatch per item on the count distribution, none per draw.
