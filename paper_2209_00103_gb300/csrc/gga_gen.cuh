@@ -404,8 +404,10 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
     // Element m of virtual thread i in round k: va * gid + vb * round + vc * m
     // (a 4-byte element keeps the low 32 bits, which 32-bit arithmetic gives
     // exactly).
-    const V vr = static_cast<V>(g.va) * static_cast<V>(gfirst) +
-                 static_cast<V>(g.vb) * static_cast<V>(static_cast<uint64_t>(g.round0) + r0);
+    // The value parameters in registers: g may live in shared memory, where
+    // the stage stores below could alias it and force a reload per element.
+    const V va = static_cast<V>(g.va), vb = static_cast<V>(g.vb), vc = static_cast<V>(g.vc);
+    const V vr = va * static_cast<V>(gfirst) + vb * static_cast<V>(static_cast<uint64_t>(g.round0) + r0);
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       const uint32_t ex = sh.wt[j][warp] + inc[j] - pk[j];
@@ -423,15 +425,15 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
             c = (cw[KV > 1 ? q / 4 : 0] >> (8 * (q % 4))) & 0xFFu;
           }
           before += c;
-          V val = vr + static_cast<V>(g.va) * static_cast<V>(i) + static_cast<V>(g.vb) * static_cast<V>(k);
+          V val = vr + va * static_cast<V>(i) + vb * static_cast<V>(k);
           if (whole && DIST >= 0 && max_count<DIST>() > 0 && max_count<DIST>() <= 2) {
             // At most two elements: predicated stores, no loop.
             if (c > 0) stage[st + shv] = gen_value<E>(val);
-            if (max_count<DIST>() > 1 && c > 1) stage[st + 1 + shv] = gen_value<E>(val + static_cast<V>(g.vc));
+            if (max_count<DIST>() > 1 && c > 1) stage[st + 1 + shv] = gen_value<E>(val + vc);
           } else if (whole) {
-            for (uint32_t m = 0; m < c; ++m, val += static_cast<V>(g.vc)) stage[st + m + shv] = gen_value<E>(val);
+            for (uint32_t m = 0; m < c; ++m, val += vc) stage[st + m + shv] = gen_value<E>(val);
           } else {
-            for (uint32_t m = 0; m < c; ++m, val += static_cast<V>(g.vc)) {
+            for (uint32_t m = 0; m < c; ++m, val += vc) {
               const uint32_t q = st + m;
               if (q >= commit) break;
               if (staged) {
