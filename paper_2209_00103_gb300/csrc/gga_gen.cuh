@@ -408,6 +408,10 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
     // the stage stores below could alias it and force a reload per element.
     const V va = static_cast<V>(g.va), vb = static_cast<V>(g.vb), vc = static_cast<V>(g.vc);
     const V vr = va * static_cast<V>(gfirst) + vb * static_cast<V>(static_cast<uint64_t>(g.round0) + r0);
+    // Counts without a small bound, two virtual threads per thread (below):
+    // one store loop over the run of both.  (With four the switch points
+    // cost registers the kernels do not have.)
+    constexpr bool kMergedRun = KV == 2 && !(DIST >= 0 && max_count<DIST>() > 0 && max_count<DIST>() <= 2);
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
       const uint32_t ex = sh.wt[j][warp] + inc[j] - pk[j];
@@ -416,6 +420,32 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
         const uint32_t k = 2 * j + h;
         uint32_t st = sh.rb[k] + ((ex >> (16 * h)) & 0xFFFFu);
         const uint32_t csum = (pk[j] >> (16 * h)) & 0xFFFFu;
+        if (kMergedRun && whole) {
+          // The thread's virtual threads own consecutive positions of the
+          // round, so their elements form one run of csum positions from
+          // st: one loop over the run, moving to the next virtual thread's
+          // values at its first position (an empty virtual thread's switch
+          // point equals the next one's, and the later switch wins).  One
+          // shared-memory store per warp iteration over the run, against one
+          // per iteration of each virtual thread's own loop.
+          uint32_t sw[KV > 1 ? KV - 1 : 1];
+          uint32_t acc = 0;
+#pragma unroll
+          for (int i = 0; i < KV - 1; ++i) {
+            const int q = static_cast<int>(k) * (KV - 1) + i;
+            acc += (cw[q / 4] >> (8 * (q % 4))) & 0xFFu;
+            sw[i] = acc;
+          }
+          const V v0 = vr + vb * static_cast<V>(k);
+          V val = v0;
+          for (uint32_t m = 0; m < csum; ++m, val += vc) {
+#pragma unroll
+            for (int i = 0; i < KV - 1; ++i)
+              if (m == sw[i]) val = v0 + va * static_cast<V>(i + 1);
+            stage[st + m + shv] = gen_value<E>(val);
+          }
+          continue;
+        }
         uint32_t before = 0;   // elements of the earlier virtual threads of this round
 #pragma unroll
         for (int i = 0; i < KV; ++i) {
