@@ -149,7 +149,10 @@ __device__ __forceinline__ V warp_incl_scan(V v) {
 // 128-bit store (a group never straddles buckets when B is a multiple of
 // 16 / sizeof(T), and buckets start on 256-byte boundaries); the partial
 // groups at the run's ends go element by element.  The buckets are those
-// of `tab` (the LFVector's bucket table), already allocated.
+// of `tab` (the LFVector's bucket table), already allocated.  Each thread
+// keeps the bucket its last group fell in (first position, end, address)
+// and looks the table up again only when its positions pass that bucket's
+// end.
 
 template <class T>
 __device__ __forceinline__ void stage_to_buckets(const uint64_t* tab, uint32_t log2B, uint64_t B, uint64_t base,
@@ -160,14 +163,20 @@ __device__ __forceinline__ void stage_to_buckets(const uint64_t* tab, uint32_t l
   const bool group_ok = B >= VEC;
   const uint64_t gbeg = base - shv;
   const uint32_t nvec = (n + shv + VEC - 1) / VEC;
+  uint64_t cfirst = 0, cend = 0, caddr = 0;   // the bucket of this thread's last group
   for (uint32_t vi = t; vi < nvec; vi += nt) {
     const uint64_t p = gbeg + static_cast<uint64_t>(vi) * VEC;
     const uint32_t lo = vi * VEC;   // stage index of position p
     if (group_ok && lo >= shv && lo + VEC <= n + shv) {
-      uint32_t bb;
-      uint64_t off;
-      bucket_of(p, log2B, bb, off);
-      __stcs(reinterpret_cast<uint4*>(tab[bb] + off * sizeof(T)), stage4[vi]);
+      if (p < cfirst || p >= cend) {
+        uint32_t bb;
+        uint64_t off;
+        bucket_of(p, log2B, bb, off);
+        cfirst = p - off;
+        cend = cfirst + bucket_len(bb, log2B);
+        caddr = tab[bb];
+      }
+      __stcs(reinterpret_cast<uint4*>(caddr + (p - cfirst) * sizeof(T)), stage4[vi]);
     } else {
 #pragma unroll
       for (uint32_t e = 0; e < VEC; ++e) {

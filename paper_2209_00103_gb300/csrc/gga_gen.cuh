@@ -252,19 +252,27 @@ struct GenShared {
   uint32_t commit, nb;
   int stop;                   // 1: pool exhausted, 2: target reached
   uint64_t tab[kMaxBuckets];  // the LFVector's bucket table (copy)
-  // Threshold counts (ascending thresholds): ptab[i] = #{k : thr[k] <= i * 2^24},
-  // so a draw u in [i * 2^24, (i + 1) * 2^24) counts ptab[i] plus the few
-  // thresholds inside its interval.
+  // Threshold counts (ascending thresholds) per interval of 2^24 draws:
+  // ptab[i] holds c_i = #{k : thr[k] <= i * 2^24} in its top 7 bits and, in
+  // its low 25, the offset of the next threshold thr[c_i] from i * 2^24 when
+  // that threshold lies inside the interval, else 2^24 (no draw of the
+  // interval reaches it).  A draw u of interval i counts c_i when its low 24
+  // bits stay below that offset -- one table load -- and otherwise steps
+  // over the thresholds from c_i + 1.
   uint32_t thr[GGA_MAX_THRESHOLDS];
-  uint8_t ptab[256];
+  uint32_t ptab[256];
 };
 
 // Count of draw u (the high word) against ascending thresholds through the
 // table: start from the thresholds below u's interval of 2^24, then step
 // over those inside it.  Equal to #{k < nthr : u >= thr[k]}.
 __device__ __forceinline__ uint32_t table_count(const GenShared& sh, uint32_t nthr, uint32_t u) {
-  uint32_t c = sh.ptab[u >> 24];
-  while (c < nthr && u >= sh.thr[c]) ++c;
+  const uint32_t e = sh.ptab[u >> 24];
+  uint32_t c = e >> 25;
+  if ((u & 0xFFFFFFu) >= (e & 0x1FFFFFFu)) {
+    ++c;
+    while (c < nthr && u >= sh.thr[c]) ++c;
+  }
   return c;
 }
 
@@ -304,7 +312,9 @@ __device__ uint32_t grow_passes(const ArrayView& v, const GenParams& g, uint32_t
     for (uint32_t i = t0; i < 256; i += NT) {
       uint32_t c = 0;
       for (uint32_t k = 0; k < g.nthr; ++k) c += g.thr[k] <= (i << 24) ? 1u : 0u;
-      sh.ptab[i] = static_cast<uint8_t>(c);
+      const uint64_t lo = static_cast<uint64_t>(i) << 24;
+      const uint32_t rel = c < g.nthr && g.thr[c] < lo + (1u << 24) ? static_cast<uint32_t>(g.thr[c] - lo) : (1u << 24);
+      sh.ptab[i] = (c << 25) | rel;
     }
   }
   __syncthreads();
