@@ -111,10 +111,12 @@ __global__ void __launch_bounds__(256) write_kernel(ArrayView v, const uint64_t*
 //   scatter: a tile of writes is sorted by bin in shared memory (counting
 //            sort) and written as runs of (global index, value) into the bins
 //   apply:   the pairs are translated (global index -> element address) and
-//            stored, in bin order
+//            stored, in bin order, each bin's memory streamed into L2 by bulk
+//            prefetches issued a few bins ahead
 // Writes with the same index keep one of their values, as in the direct path.
-// Measured on GB300 for 2^26 int32 writes: 1.55 ms binned against 2.6 ms for
-// a direct scatter (flat array, same indices).
+// Measured on GB300 for 2^26 int32 writes: 1.53-1.55 ms binned (1.71 ms
+// without the prefetch) against 2.0-2.6 ms for a direct scatter (flat array,
+// same indices).
 
 constexpr uint32_t kWbinMaxBins = 256;
 constexpr uint64_t kWbinMin = 1ull << 20;        // smaller batches write directly
@@ -267,6 +269,48 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_scatter_kernel(ArrayView v,
   }
 }
 
+// Brings the array's elements of global indices [g0, g1) into L2, by warp
+// 0 of the block (every lane calls it): lane i walks LFVectors l0 + i,
+// l0 + i + 32, ... of the range (l0 found once), one bulk prefetch per run
+// (one bucket of one LFVector), widened to 16-byte boundaries inside the
+// bucket's allocation.
+template <int E>
+__device__ void prefetch_range_l2_warp(const ArrayView& v, uint64_t N, uint64_t g0, uint64_t g1) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint32_t l0 = 0;
+  if (lane == 0) l0 = find_lfv(v.offsets, v.L, N, g0);
+  l0 = __shfl_sync(0xffffffffu, l0, 0);
+  constexpr uint64_t kMaxPrefetch = static_cast<uint64_t>(1) << 30;
+  for (uint32_t l = l0 + lane; l < v.L; l += 32) {
+    const uint64_t lo = __ldg(v.offsets + l), hi = __ldg(v.offsets + l + 1);
+    if (lo >= g1) break;   // offsets ascend: so do the later LFVectors of this lane
+    uint64_t j = (g0 > lo ? g0 : lo) - lo;
+    const uint64_t jend = (g1 < hi ? g1 : hi) - lo;
+    while (j < jend) {
+      uint32_t b;
+      uint64_t o;
+      bucket_of(j, v.log2B, b, o);
+      const uint64_t run = min(bucket_len(b, v.log2B) - o, jend - j);
+      const uint64_t base = __ldg(v.buckets + static_cast<uint64_t>(l) * kMaxBuckets + b);
+      const uint64_t a0 = (base + o * E) & ~15ull, a1 = (base + (o + run) * E + 15) & ~15ull;
+      for (uint64_t a = a0; a < a1; a += kMaxPrefetch)
+        bulk_prefetch_l2(reinterpret_cast<const void*>(a),
+                         static_cast<uint32_t>(a1 - a < kMaxPrefetch ? a1 - a : kMaxPrefetch));
+      j += run;
+    }
+  }
+}
+
+// Bins fetched ahead: the block whose tile holds the first write of bin b
+// prefetches the bin kWbinAheadBytes of array further on (blocks 0, 1, ...
+// the bins before it, one each), so that a bin's sectors come from DRAM as
+// one stream instead of one random fill per first write to each.  Measured on
+// GB300 for 2^26 int32 writes into 2^28 elements (8 MB bins; write phase):
+// no prefetch 1.71 ms, 2 bins ahead 1.65, 4 1.59, 8 1.53-1.55, 12 1.64,
+// 16 1.79, 24 2.13 (the bins then no longer stay in the 129 MB L2 until
+// their writes arrive).
+constexpr uint64_t kWbinAheadBytes = 64ull << 20;
+
 template <int E>
 __global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, const uint64_t* __restrict__ gidx,
                                                                   const typename Elem<E>::T* __restrict__ val,
@@ -275,6 +319,33 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, c
   constexpr int kPer = WbinTile<E>::kPer;
   const uint64_t total = *wbin_valid(scr);
   const uint64_t N = __ldg(v.offsets + v.L);
+  if (threadIdx.x < 32 && N > 0) {   // warp 0: the prefetches of this tile
+    const uint32_t shift = wbin_shift(N, E);
+    const uint32_t nbins = static_cast<uint32_t>(((N - 1) >> shift) + 1);
+    const uint64_t bin_bytes = static_cast<uint64_t>(E) << shift;
+    const uint32_t ahead = bin_bytes >= kWbinAheadBytes ? 1u : static_cast<uint32_t>(kWbinAheadBytes / bin_bytes);
+    // Blocks 0 .. ahead - 1 fetch the first bins, one each.
+    if (blockIdx.x < ahead && blockIdx.x < nbins)
+      prefetch_range_l2_warp<E>(v, N, static_cast<uint64_t>(blockIdx.x) << shift,
+                                min(static_cast<uint64_t>(blockIdx.x + 1) << shift, N));
+    const unsigned long long* ends = wbin_cursors(scr);   // advanced to the bin ends by the scatter
+    const uint64_t t0 = static_cast<uint64_t>(blockIdx.x) * kWbinThreads * kPer;
+    const uint64_t t1 = t0 + static_cast<uint64_t>(kWbinThreads) * kPer;
+    // First bin starting at or after t0 (bin starts ascend): binary search.
+    uint32_t lo = 0, hi = nbins;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if ((mid ? ends[mid - 1] : 0) < t0) lo = mid + 1;
+      else hi = mid;
+    }
+    for (uint32_t b = lo; b < nbins; ++b) {
+      const uint64_t start = b ? ends[b - 1] : 0;
+      if (start >= t1) break;
+      const uint32_t pb = b + ahead;   // this tile holds bin b's first write
+      if (ends[b] != start && pb < nbins)
+        prefetch_range_l2_warp<E>(v, N, static_cast<uint64_t>(pb) << shift, min(static_cast<uint64_t>(pb + 1) << shift, N));
+    }
+  }
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWbinThreads * kPer;
   for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kWbinThreads * kPer; base < total; base += stride) {
     uint64_t a[kPer];
