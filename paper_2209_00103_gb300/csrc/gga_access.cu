@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) write_kernel(ArrayView v, const uint64_t*
 //            stored, in bin order, each bin's memory streamed into L2 by bulk
 //            prefetches issued a few bins ahead
 // Writes with the same index keep one of their values, as in the direct path.
-// Measured on GB300 for 2^26 int32 writes: 1.53-1.55 ms binned (1.71 ms
+// Measured on GB300 for 2^26 int32 writes: 1.44-1.46 ms binned (1.71 ms
 // without the prefetch) against 2.0-2.6 ms for a direct scatter (flat array,
 // same indices).
 
@@ -305,10 +305,11 @@ __device__ void prefetch_range_l2_warp(const ArrayView& v, uint64_t N, uint64_t 
 // prefetches the bin kWbinAheadBytes of array further on (blocks 0, 1, ...
 // the bins before it, one each), so that a bin's sectors come from DRAM as
 // one stream instead of one random fill per first write to each.  Measured on
-// GB300 for 2^26 int32 writes into 2^28 elements (8 MB bins; write phase):
-// no prefetch 1.71 ms, 2 bins ahead 1.65, 4 1.59, 8 1.53-1.55, 12 1.64,
-// 16 1.79, 24 2.13 (the bins then no longer stay in the 129 MB L2 until
-// their writes arrive).
+// GB300 for 2^26 int32 writes into 2^28 elements (8 MB bins; write phase,
+// ranges walked by one thread): no prefetch 1.71 ms, 2 bins ahead 1.65, 4
+// 1.59, 8 1.53-1.55, 12 1.64, 16 1.79, 24 2.13 (the bins then no longer stay
+// in the 129 MB L2 until their writes arrive); 8 bins walked by warp 0:
+// 1.44-1.46 ms.
 constexpr uint64_t kWbinAheadBytes = 64ull << 20;
 
 template <int E>
