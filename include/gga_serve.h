@@ -4,8 +4,9 @@
  * and 2 through gga_append_batch, read = Sec. IV's global indexing through
  * gga_read_batch, flatten = the contiguous copy, after which the array is
  * retired with gga_clear).  The paper has no server; this is the host-side
- * scheduler of the benchmark spec's serving pattern, written natively so that
- * the host's per-request work stays small next to the GPU's.
+ * scheduler of a serving workload (continuous batching of requests against
+ * many live arrays), written natively so that the host's per-request work
+ * stays small next to the GPU's.
  *
  * The scheduling rules (also the rules of the Python reference model in
  * paper_2209_00103_gb300/serving.py, which is tested on the CPU):

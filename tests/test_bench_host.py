@@ -1,7 +1,7 @@
 """bench.py's host logic: the recorded DRAM traffic is used only while the
 kernel's source still matches the hash stored with it, the algorithmic bytes
-follow their per-unit definitions, and the measured peaks are read from the
-driver's file when it is there."""
+follow their per-unit definitions, and the measured peaks are read from
+MEASURED_PEAKS.json when it is there."""
 
 import os
 
