@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(256) write_kernel(ArrayView v, const uint64_t*
 // first grouped by ranges of global indices ("bins" of ~8 MB of elements) and
 // then applied bin after bin, so the writes that share a sector meet while it
 // is held in L2: each touched sector is fetched and written back once.
-//   count:   per-bin totals (block histogram, one global atomic per bin per block)
+//   count:   per-bin totals (block histogram over the tiles the block takes,
+//            one global atomic per bin per block)
 //   scan:    bin cursors = exclusive scan of the totals; totals reset
 //   scatter: a tile of writes is sorted by bin in shared memory (counting
 //            sort) and written as runs of (global index, value) into the bins
@@ -154,15 +155,22 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_count_kernel(ArrayView v, c
   const uint32_t shift = wbin_shift(N, E);
   for (uint32_t b = threadIdx.x; b < kWbinMaxBins; b += blockDim.x) h[b] = 0;
   __syncthreads();
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kWbinThreads * kPer;
   bool bad = false;
+  // Tiles of kWbinThreads * kPer indices, taken by the blocks in turn: a
+  // tile's indices are all loaded before any is counted.
+  const uint64_t tile = static_cast<uint64_t>(kWbinThreads) * kPer;
+  for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * tile; base < n;
+       base += static_cast<uint64_t>(gridDim.x) * tile) {
+    uint64_t g[kPer];
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
-    if (i < n) {
-      const uint64_t g = __ldcs(idx + i);
-      if (g < N) atomicAdd(&h[static_cast<uint32_t>(g >> shift)], 1u);
-      else bad = true;
+    for (int u = 0; u < kPer; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
+      g[u] = i < n ? __ldcs(idx + i) : ~0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      if (g[u] < N) atomicAdd(&h[static_cast<uint32_t>(g[u] >> shift)], 1u);
+      else if (g[u] != ~0ull) bad = true;
     }
   }
   if (bad) latch_error(v.status, GGA_ERR_OUT_OF_RANGE);
@@ -753,7 +761,18 @@ static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const 
   const unsigned grid = static_cast<unsigned>(tiles > 0x7FFFFFFFull ? 0x7FFFFFFFull : tiles);
   const int smem = kTile * (8 + E + 1);
   cudaFuncSetAttribute(wbin_scatter_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  wbin_count_kernel<E><<<grid, kWbinThreads, 0, st>>>(v, idx, n, scr);
+  // The count runs 4 blocks per SM that take the tiles in turn (one set of
+  // global bin additions per block): measured on GB300 for 2^26 int32
+  // writes, write phase 1.408 ms against 1.460 ms with one block per tile.
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const uint64_t cgrid_cap = static_cast<uint64_t>(sms) * 4;
+  const unsigned cgrid = grid > cgrid_cap ? static_cast<unsigned>(cgrid_cap) : grid;
+  wbin_count_kernel<E><<<cgrid, kWbinThreads, 0, st>>>(v, idx, n, scr);
   wbin_scan_kernel<<<1, kWbinMaxBins, 0, st>>>(scr);
   wbin_scatter_kernel<E><<<grid, kWbinThreads, smem, st>>>(v, idx, static_cast<const T*>(in), n, scr, out_idx,
                                                            out_val);
