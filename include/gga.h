@@ -289,7 +289,7 @@ int gga_read(gga_handle h, const uint64_t* idx_dev, uint64_t n, void* out_dev, v
  * index >= size latches GGA_ERR_OUT_OF_RANGE and is skipped.  A batch of
  * 2^20 writes or more is grouped by ranges of global indices first and
  * applied range by range (the writes that share a 32-byte sector then meet
- * in L2); its bins, (8 + E) * n + 4 KB bytes of device memory, are allocated
+ * in L2); its bins, (4 + E) * n + 4 KB bytes of device memory, are allocated
  * stream-ordered on the first such call and kept by the handle (reused and
  * grown by later calls, freed by gga_destroy).  If they cannot be allocated
  * the writes go directly.

@@ -110,22 +110,26 @@ __global__ void __launch_bounds__(256) write_kernel(ArrayView v, const uint64_t*
 //            one global atomic per bin per block)
 //   scan:    bin cursors = exclusive scan of the totals; totals reset
 //   scatter: a tile of writes is sorted by bin in shared memory (counting
-//            sort) and written as runs of (global index, value) into the bins
-//   apply:   the pairs are translated (global index -> element address) and
+//            sort) and written as runs of (offset inside the bin, value) into
+//            the bins: 4 + E bytes per write instead of 8 + E
+//   apply:   each pair's global index (its bin, found from the bin ends, and
+//            the offset) is translated to an element address and the value
 //            stored, in bin order, each bin's memory streamed into L2 by bulk
 //            prefetches issued a few bins ahead
 // Writes with the same index keep one of their values, as in the direct path.
-// Measured on GB300 for 2^26 int32 writes: 1.44-1.46 ms binned (1.71 ms
-// without the prefetch) against 2.0-2.6 ms for a direct scatter (flat array,
-// same indices).
+// Measured on GB300 for 2^26 int32 writes: 1.22 ms binned (1.41 ms with
+// 64-bit global indices in the bins, 1.71 ms without the prefetch either)
+// against 2.0-2.6 ms for a direct scatter (flat array, same indices).
 
 constexpr uint32_t kWbinMaxBins = 256;
 constexpr uint64_t kWbinMin = 1ull << 20;        // smaller batches write directly
 constexpr uint64_t kWbinHeader = 4096;           // totals[256] u32 | cursors[256] u64 | valid u64
 constexpr int kWbinThreads = 256;
 
-// Values follow the addresses in the scratch, 256-byte aligned.
-uint64_t wbin_values_offset(uint64_t n) { return (kWbinHeader + n * 8 + 255) & ~255ull; }
+// The bins hold, per write, the element's offset inside its bin (32 bits:
+// a bin spans at most 2^32 elements, 2^shift with shift <= 32 for any array
+// below 2^40 elements) and then, 256-byte aligned, the values.
+uint64_t wbin_values_offset(uint64_t n) { return (kWbinHeader + n * 4 + 255) & ~255ull; }
 
 template <int E> struct WbinTile { static constexpr int kPer = 16; };
 template <> struct WbinTile<16> { static constexpr int kPer = 8; };
@@ -204,7 +208,7 @@ __global__ void __launch_bounds__(kWbinMaxBins) wbin_scan_kernel(uint8_t* scr) {
 template <int E>
 __global__ void __launch_bounds__(kWbinThreads) wbin_scatter_kernel(ArrayView v, const uint64_t* __restrict__ idx,
                                                                     const typename Elem<E>::T* __restrict__ in,
-                                                                    uint64_t n, uint8_t* scr, uint64_t* out_idx,
+                                                                    uint64_t n, uint8_t* scr, uint32_t* out_off,
                                                                     typename Elem<E>::T* out_val) {
   typedef typename Elem<E>::T T;
   constexpr int kPer = WbinTile<E>::kPer;
@@ -214,11 +218,15 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_scatter_kernel(ArrayView v,
   __shared__ unsigned long long gbase[kWbinMaxBins];
   __shared__ uint32_t wsum[kWbinThreads / 32];
   extern __shared__ __align__(16) uint8_t s_dyn[];
-  uint64_t* s_idx = reinterpret_cast<uint64_t*>(s_dyn);
-  T* s_val = reinterpret_cast<T*>(s_dyn + static_cast<size_t>(kTile) * 8);
-  uint8_t* s_bin = s_dyn + static_cast<size_t>(kTile) * (8 + E);
+  T* s_val = reinterpret_cast<T*>(s_dyn);
+  uint32_t* s_off = reinterpret_cast<uint32_t*>(s_dyn + static_cast<size_t>(kTile) * E);
+  uint8_t* s_bin = s_dyn + static_cast<size_t>(kTile) * (4 + E);
   const uint64_t N = __ldg(v.offsets + v.L);
   const uint32_t shift = wbin_shift(N, E);
+  if (shift > 32) {   // bins past 2^32 elements: arrays of 2^40 elements and more
+    if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(v.status, GGA_ERR_INVALID);
+    return;
+  }
   for (uint32_t b = threadIdx.x; b < kWbinMaxBins; b += blockDim.x) h[b] = 0;
   __syncthreads();
   const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile;
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_scatter_kernel(ArrayView v,
     if (g[u] == ~0ull) continue;
     const uint32_t b = static_cast<uint32_t>(g[u] >> shift);
     const uint32_t p = off[b] + rank[u];
-    s_idx[p] = g[u];
+    s_off[p] = static_cast<uint32_t>(g[u] - (static_cast<uint64_t>(b) << shift));
     s_val[p] = x[u];
     s_bin[p] = static_cast<uint8_t>(b);
   }
@@ -272,7 +280,7 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_scatter_kernel(ArrayView v,
   for (uint32_t p = threadIdx.x; p < valid; p += blockDim.x) {
     const uint32_t b = s_bin[p];
     const unsigned long long q = gbase[b] + (p - off[b]);
-    out_idx[q] = s_idx[p];
+    out_off[q] = s_off[p];
     out_val[q] = s_val[p];
   }
 }
@@ -321,7 +329,7 @@ __device__ void prefetch_range_l2_warp(const ArrayView& v, uint64_t N, uint64_t 
 constexpr uint64_t kWbinAheadBytes = 64ull << 20;
 
 template <int E>
-__global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, const uint64_t* __restrict__ gidx,
+__global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, const uint32_t* __restrict__ goff,
                                                                   const typename Elem<E>::T* __restrict__ val,
                                                                   uint8_t* scr) {
   typedef typename Elem<E>::T T;
@@ -355,23 +363,48 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, c
         prefetch_range_l2_warp<E>(v, N, static_cast<uint64_t>(pb) << shift, min(static_cast<uint64_t>(pb + 1) << shift, N));
     }
   }
+  if (N == 0) return;
+  const uint32_t shift = wbin_shift(N, E);
+  const uint32_t nbins = static_cast<uint32_t>(((N - 1) >> shift) + 1);
+  const unsigned long long* ends = wbin_cursors(scr);   // advanced to the bin ends by the scatter
+  const uint32_t lane = threadIdx.x & 31;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * kWbinThreads * kPer;
   for (uint64_t base = static_cast<uint64_t>(blockIdx.x) * kWbinThreads * kPer; base < total; base += stride) {
-    uint64_t a[kPer];
+    uint32_t o[kPer];
     T x[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
-      a[u] = 0;
+      o[u] = 0;
       if (i < total) {
-        a[u] = __ldcs(gidx + i);
+        o[u] = __ldcs(goff + i);
         x[u] = __ldcs(val + i);
       }
     }
+    // The bin of the tile's first write (lane 0 searches the bin ends while
+    // the loads above are in flight); a write's bin is that one or, past its
+    // end, one of the next (the tile's writes are in bin order).
+    uint32_t bf = 0;
+    if (lane == 0) {
+      uint32_t lo = 0, hi = nbins;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (ends[mid] <= base) lo = mid + 1;
+        else hi = mid;
+      }
+      bf = lo;
+    }
+    uint32_t b = __shfl_sync(0xffffffffu, bf, 0);
+    unsigned long long e = ends[b];   // the thread's positions ascend with u: b only moves forward
 #pragma unroll
-    for (int u = 0; u < kPer; ++u)
-      if (base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x < total)
-        *reinterpret_cast<T*>(element_addr(v, N, a[u])) = x[u];
+    for (int u = 0; u < kPer; ++u) {
+      const uint64_t i = base + static_cast<uint64_t>(u) * kWbinThreads + threadIdx.x;
+      if (i < total) {
+        while (i >= e) e = ends[++b];
+        const uint64_t g = (static_cast<uint64_t>(b) << shift) + o[u];
+        *reinterpret_cast<T*>(element_addr(v, N, g)) = x[u];
+      }
+    }
   }
 }
 
@@ -755,11 +788,11 @@ static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const 
   }
   constexpr int kTile = kWbinThreads * WbinTile<E>::kPer;
   uint8_t* scr = static_cast<uint8_t*>(scratch);
-  uint64_t* out_idx = reinterpret_cast<uint64_t*>(scr + kWbinHeader);
+  uint32_t* out_off = reinterpret_cast<uint32_t*>(scr + kWbinHeader);
   T* out_val = reinterpret_cast<T*>(scr + wbin_values_offset(n));
   const uint64_t tiles = (n + kTile - 1) / kTile;
   const unsigned grid = static_cast<unsigned>(tiles > 0x7FFFFFFFull ? 0x7FFFFFFFull : tiles);
-  const int smem = kTile * (8 + E + 1);
+  const int smem = kTile * (4 + E + 1);
   cudaFuncSetAttribute(wbin_scatter_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   // The count runs 4 blocks per SM that take the tiles in turn (one set of
   // global bin additions per block): measured on GB300 for 2^26 int32
@@ -774,9 +807,9 @@ static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const 
   const unsigned cgrid = grid > cgrid_cap ? static_cast<unsigned>(cgrid_cap) : grid;
   wbin_count_kernel<E><<<cgrid, kWbinThreads, 0, st>>>(v, idx, n, scr);
   wbin_scan_kernel<<<1, kWbinMaxBins, 0, st>>>(scr);
-  wbin_scatter_kernel<E><<<grid, kWbinThreads, smem, st>>>(v, idx, static_cast<const T*>(in), n, scr, out_idx,
+  wbin_scatter_kernel<E><<<grid, kWbinThreads, smem, st>>>(v, idx, static_cast<const T*>(in), n, scr, out_off,
                                                            out_val);
-  wbin_apply_kernel<E><<<grid, kWbinThreads, 0, st>>>(v, out_idx, out_val, scr);
+  wbin_apply_kernel<E><<<grid, kWbinThreads, 0, st>>>(v, out_off, out_val, scr);
 }
 
 int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st) {
