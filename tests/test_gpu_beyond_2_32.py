@@ -3,8 +3,8 @@
 global indices, offsets and flatten positions need 64 bits.  Three
 LFVectors -- the first, one in the middle and the last, whose elements lie
 past global index 2^32 -- are rebuilt by the oracle from their own draws;
-sizes, capacities, sampled reads, writes, both sweeps and the flattened
-array are checked against it."""
+sizes, capacities, sampled reads, writes (direct, and a batch large enough
+to be binned), both sweeps and the flattened array are checked against it."""
 
 import numpy as np
 import pytest
@@ -69,6 +69,32 @@ def test_generated_array_beyond_2_32_elements():
     g.write(gidx[L - 1], torch.from_numpy(newv).cuda())
     assert np.array_equal(g.read(gidx[L - 1]).cpu().numpy(), newv)
     picks[L - 1] = (j, newv.view(np.uint32) - np.uint32(3), None)
+    # A batch of 2^20 + 5 writes (the binned path: writes grouped by ranges of
+    # global indices, each stored as its bin and its offset inside the bin)
+    # into the three checked LFVectors, the last of them past 2^32; the
+    # values are keyed by the index, so repeated indices agree.
+    rng2 = np.random.default_rng(9)
+    ls = np.array(sorted(picks), dtype=np.int64)
+    nw = (1 << 20) + 5
+    li = rng2.integers(0, ls.size, nw)
+    loc = (rng2.random(nw) * sizes[ls[li]]).astype(np.int64)
+    gw = offs[ls[li]] + loc
+    assert gw.max() >= (1 << 32)
+    vals = ((gw.astype(np.uint64) * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    gw_dev = torch.from_numpy(gw).cuda()
+    g.write(gw_dev, torch.from_numpy(vals.view(np.int32)).cuda())
+    assert np.array_equal(g.read(gw_dev).cpu().numpy().view(np.uint32), vals)
+    for l, (j, want, o) in list(picks.items()):
+        m = ls[li] == l
+        hit = dict(zip(loc[m].tolist(), vals[m].tolist()))
+        w2 = want.copy()
+        for k, jj in enumerate(j.tolist()):
+            if jj in hit:
+                w2[k] = np.uint32((hit[jj] - 3) & 0xFFFFFFFF)
+        picks[l] = (j, w2, o)
+    for l, (j, want, _) in picks.items():   # the sampled positions: written or kept
+        got = g.read(gidx[l]).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want + np.uint32(3)), l
     # Flatten: the sampled positions of the contiguous copy.
     dst = gga.elem_tensor(n, E)
     g.flatten(dst)
