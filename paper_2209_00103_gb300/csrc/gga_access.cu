@@ -133,6 +133,9 @@ uint64_t wbin_values_offset(uint64_t n) { return (kWbinHeader + n * 4 + 255) & ~
 
 template <int E> struct WbinTile { static constexpr int kPer = 16; };
 template <> struct WbinTile<16> { static constexpr int kPer = 8; };
+// Writes per thread in the apply (its own tiles): measured on GB300 for 2^26
+// int32 writes, write phase 1.190 ms at 8, 1.204 ms at 16, 1.299 ms at 32.
+template <int E> struct WbinApplyPer { static constexpr int kPer = 8; };
 
 // Bin of global index g: g >> shift, with 2^shift elements ~ 8 MB, raised
 // until at most kWbinMaxBins bins cover [0, N).
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(kWbinThreads) wbin_apply_kernel(ArrayView v, c
                                                                   const typename Elem<E>::T* __restrict__ val,
                                                                   uint8_t* scr) {
   typedef typename Elem<E>::T T;
-  constexpr int kPer = WbinTile<E>::kPer;
+  constexpr int kPer = WbinApplyPer<E>::kPer;
   const uint64_t total = *wbin_valid(scr);
   const uint64_t N = __ldg(v.offsets + v.L);
   if (threadIdx.x < 32 && N > 0) {   // warp 0: the prefetches of this tile
@@ -809,7 +812,10 @@ static void write_as(const ArrayView& v, const uint64_t* idx, uint64_t n, const 
   wbin_scan_kernel<<<1, kWbinMaxBins, 0, st>>>(scr);
   wbin_scatter_kernel<E><<<grid, kWbinThreads, smem, st>>>(v, idx, static_cast<const T*>(in), n, scr, out_off,
                                                            out_val);
-  wbin_apply_kernel<E><<<grid, kWbinThreads, 0, st>>>(v, out_off, out_val, scr);
+  constexpr int kTileA = kWbinThreads * WbinApplyPer<E>::kPer;
+  const uint64_t tiles_a = (n + kTileA - 1) / kTileA;
+  const unsigned grid_a = static_cast<unsigned>(tiles_a > 0x7FFFFFFFull ? 0x7FFFFFFFull : tiles_a);
+  wbin_apply_kernel<E><<<grid_a, kWbinThreads, 0, st>>>(v, out_off, out_val, scr);
 }
 
 int launch_read(const ArrayView& v, const uint64_t* idx, uint64_t n, void* out, int num_sms, cudaStream_t st) {
